@@ -1,0 +1,150 @@
+/*
+ * jp.h -- C-ABI of the GB300 join-project library (libjp.so).
+ *
+ * The library evaluates, on one GPU, the two join-project queries of
+ * "Fast Join Project Query Evaluation using Matrix Multiplication"
+ * (Deep, Hu, Koutris):
+ *
+ *   two-path (Section 2.1)   Q(x,z)         = R(x,y), S(z,y)
+ *   star     (Section 2.1)   Q*_k(x1..xk)   = R1(x1,y), ..., Rk(xk,y)
+ *
+ * with set semantics (SELECT DISTINCT, Example 1).  Both follow the
+ * heavy/light split of Algorithm 1 (Section 3.1) and of the star algorithm
+ * (Section 3.2): tuples with a light value are joined by a worst-case optimal
+ * expansion over CSR neighbour lists and deduplicated per x; tuples whose
+ * values are all heavy become 0/1 matrices whose product (Section 2.2,
+ * "Join-Project as Matrix Multiplication") runs on the tensor cores; the two
+ * parts are united per output row.  The result is exact: every distinct
+ * tuple, sorted lexicographically as signed int32, with no approximation.
+ *
+ * Conventions shared by every entry point:
+ *  - All pointers in jp_rel are DEVICE pointers, or HOST pointers (pageable
+ *    or pinned), detected per call; host inputs are copied to the device
+ *    inside the call.  Inputs are borrowed for the duration of the call and
+ *    never written.  Columns are SoA int32 arrays of n entries; any int32
+ *    value is allowed (negatives included); duplicate tuples are allowed and
+ *    removed (relations are sets).
+ *  - Work is issued on the context's stream.  The calls return after the
+ *    result count is known; result columns are then ready on that stream.
+ *  - Every call returns JP_OK (0) or a negative JP_E* code and never aborts,
+ *    traps or prints.  jp_last_error() gives a one-line message.  There is
+ *    no CPU fallback: without a usable GPU the calls fail with JP_ECUDA.
+ *  - Device memory comes from the jp_alloc_fn/jp_free_fn pair given to
+ *    jp_create (the Python binding passes PyTorch's caching allocator); with
+ *    NULL the library uses stream-ordered cudaMallocAsync/cudaFreeAsync.
+ *    The context keeps a workspace between calls and grows it on demand.
+ */
+#ifndef JP_H
+#define JP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define JP_OK            0
+#define JP_EINVAL       -1   /* bad argument (NULL pointer, n < 0, k out of range, ...) */
+#define JP_ENOMEM       -2   /* the allocator returned NULL */
+#define JP_ECUDA        -3   /* a CUDA call failed (message in jp_last_error) */
+#define JP_EOVERFLOW    -4   /* a device-side capacity check failed; nothing was written out of bounds */
+#define JP_ETIMEOUT     -5   /* a bounded device-side wait ran out; the kernel stopped and returned */
+#define JP_EUNSUPPORTED -6   /* the device is not an sm_103 GPU, or a size exceeds a stated limit */
+
+/* Threshold modes for jp_set_threshold (Section 3.1, Section 5). */
+#define JP_FIXED        0    /* use the given Delta1, Delta2 (clamped to [1, N]) */
+#define JP_CLOSED_FORM  1    /* Lemma 3's minimiser of the omega = 2 cost, with the Section 5 output estimate */
+#define JP_COST_MODEL   2    /* Algorithm 3 (Section 5) with GPU-calibrated constants */
+
+typedef struct jp_ctx jp_ctx;
+
+/* One binary relation R(x, y) as two int32 columns of n entries. */
+typedef struct {
+    const int32_t* x;   /* first attribute (x, z or x_i) */
+    const int32_t* y;   /* join attribute y */
+    int64_t n;          /* number of tuples (duplicates allowed), >= 0 */
+} jp_rel;
+
+/* Query result.  col[i] holds attribute i of every output tuple (two-path:
+ * col[0] = x, col[1] = z; star: col[i] = x_{i+1}); count tuples, sorted
+ * lexicographically as signed int32.  Columns are device memory owned by the
+ * library until jp_result_free; they live in one allocation. */
+typedef struct {
+    int32_t* col[8];
+    int64_t count;
+    int32_t k;          /* number of columns */
+    void* _block;       /* library-owned allocation backing the columns */
+    size_t _bytes;
+} jp_result;
+
+/* Per-call statistics of the last query (jp_get_stats). */
+typedef struct {
+    int64_t n_r, n_s;          /* distinct tuples of R and S after normalisation */
+    int64_t dom_x, dom_y, dom_z;
+    double  out_join;          /* |OUT_join| = sum_y deg_R(y) deg_S(y) (Section 5) */
+    double  out_estimate;      /* Section 5 estimate of |OUT| */
+    int64_t delta1, delta2;    /* thresholds used */
+    int32_t threshold_mode;
+    int64_t u, v, w;           /* heavy x, heavy y, heavy z counts (matrix dims) */
+    int64_t light_candidates;  /* light join size enumerated before dedup */
+    int64_t out_count;         /* |OUT| */
+    int64_t heavy_pairs;       /* nonzeros of the heavy product (0 if not counted) */
+    int64_t kernel_launches;   /* kernels the library launched for the query */
+    double  ms_total;          /* host wall time of the call */
+    double  ms_pass[16];       /* device ms (CUDA events on the query stream) of:
+                                  0 index build, 1 threshold selection, 2 partition,
+                                  3 matrix build, 4 heavy GEMM kernel, 5 light
+                                  classification, 6-9 light kernels (warp, 2K-block,
+                                  16K-block, bitmap+union), 10 output count,
+                                  11 output placement kernel, 12 whole query */
+} jp_stats;
+
+typedef void* (*jp_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void  (*jp_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* Create a context on `device`, issuing work on `stream` (a cudaStream_t, NULL
+ * = legacy default stream).  alloc/free may both be NULL (see above).
+ * Fails with JP_EUNSUPPORTED when the device is not compute capability 10.3. */
+int jp_create(jp_ctx** ctx, int device, void* stream, jp_alloc_fn alloc, jp_free_fn release,
+              void* user);
+
+/* Release the context's workspace and the context itself (NULL is a no-op). */
+void jp_destroy(jp_ctx* ctx);
+
+/* Choose how Delta1 (y threshold) and Delta2 (x/z threshold) are picked
+ * (Section 3.1: a tuple is light when a value's degree is <= its threshold).
+ * delta1/delta2 are used in JP_FIXED mode only and must be >= 1. */
+int jp_set_threshold(jp_ctx* ctx, int mode, int64_t delta1, int64_t delta2);
+
+/* Change the stream of subsequent calls. */
+int jp_set_stream(jp_ctx* ctx, void* stream);
+
+/* Two-path query Q(x,z) = R(x,y), S(z,y) (Section 2.1, Algorithm 1).
+ * S == NULL means S = R (self-join).  On success *out holds count sorted
+ * distinct (x, z) pairs, k = 2.  R->n + S->n must stay below 2^31. */
+int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out);
+
+/* Star query Q*_k (Section 2.1, Section 3.2) over rels[0..k-1], 2 <= k <= 8;
+ * on success *out holds the sorted distinct k-tuples. */
+int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out);
+
+/* Statistics of the last successful query. */
+int jp_get_stats(const jp_ctx* ctx, jp_stats* stats);
+
+/* Copy result columns to host buffers host_cols[0..k-1] (each >= count
+ * entries; pinned memory is fastest) and wait for the copy. */
+int jp_result_to_host(jp_ctx* ctx, const jp_result* res, int32_t* const* host_cols);
+
+/* Return a result's device memory (stream-ordered) and zero *res. */
+void jp_result_free(jp_ctx* ctx, jp_result* res);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* jp_last_error(const jp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JP_H */

@@ -1,0 +1,371 @@
+// C-ABI entry points: context, workspace, argument checks and the two-path
+// pipeline of Algorithm 1 (Section 3.1):
+//   index build -> thresholds -> partition -> heavy matrices + product ->
+//   light expansion/deduplication + union -> output placement.
+#include <chrono>
+#include <cstring>
+#include <new>
+
+#include "jp_internal.cuh"
+
+struct jp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    jp::Arena ws;
+    int mode = JP_CLOSED_FORM;
+    int64_t d1 = 1, d2 = 1;
+    std::string err;
+    jp_stats stats;
+    bool have_stats = false;
+    uint32_t* hist_host = nullptr;     // pinned, 2048 entries
+    int64_t* host_scalars = nullptr;   // pinned, 64 entries
+    uint32_t* d_status = nullptr;      // device status word
+    jp::Timer tm;
+};
+
+namespace jp {
+
+int64_t g_launches = 0;
+Timer* g_timer = nullptr;
+
+void* Arena::raw_alloc(size_t bytes) {
+    if (alloc) return alloc(bytes, (void*)stream, user);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Arena::raw_free(void* p, size_t bytes) {
+    if (!p) return;
+    if (release) release(p, bytes, (void*)stream, user);
+    else cudaFreeAsync(p, stream);
+}
+
+void* Arena::carve(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    while (cur < chunks.size()) {
+        if (off + bytes <= chunks[cur].size) {
+            void* p = chunks[cur].p + off;
+            off += bytes;
+            used += bytes;
+            if (used > peak) peak = used;
+            return p;
+        }
+        ++cur;
+        off = 0;
+    }
+    size_t total = 0;
+    for (auto& c : chunks) total += c.size;
+    size_t sz = bytes;
+    if (sz < total) sz = total;
+    if (sz < ((size_t)64 << 20)) sz = (size_t)64 << 20;
+    void* p = raw_alloc(sz);
+    if (!p) throw Error{JP_ENOMEM, "workspace allocation of " + std::to_string(sz) + " bytes failed"};
+    chunks.push_back({reinterpret_cast<char*>(p), sz});
+    cur = chunks.size() - 1;
+    off = bytes;
+    used += bytes;
+    if (used > peak) peak = used;
+    return p;
+}
+
+void Arena::release_all() {
+    for (auto& c : chunks) raw_free(c.p, c.size);
+    chunks.clear();
+    reset();
+}
+
+}  // namespace jp
+
+namespace {
+
+int fail(jp_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device copy of a relation (host inputs are copied into the workspace).
+jp_rel to_device(jp_ctx* ctx, const jp_rel* r) {
+    jp_rel d = *r;
+    if (r->n == 0) return d;
+    const size_t bytes = (size_t)r->n * sizeof(int32_t);
+    if (!is_device_ptr(r->x)) {
+        int32_t* p = ctx->ws.get<int32_t>(r->n);
+        JP_CUDA_TRY(cudaMemcpyAsync(p, r->x, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        d.x = p;
+    }
+    if (!is_device_ptr(r->y)) {
+        int32_t* p = ctx->ws.get<int32_t>(r->n);
+        JP_CUDA_TRY(cudaMemcpyAsync(p, r->y, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        d.y = p;
+    }
+    return d;
+}
+
+int check_rel(jp_ctx* ctx, const jp_rel* r, const char* name) {
+    if (!r) return fail(ctx, JP_EINVAL, std::string(name) + " is NULL");
+    if (r->n < 0) return fail(ctx, JP_EINVAL, std::string(name) + "->n is negative");
+    if (r->n > 0 && (!r->x || !r->y)) return fail(ctx, JP_EINVAL, std::string(name) + " has a NULL column");
+    if (r->n >= ((int64_t)1 << 31)) return fail(ctx, JP_EUNSUPPORTED, std::string(name) + " has 2^31 or more tuples");
+    return JP_OK;
+}
+
+void status_check(jp_ctx* ctx) {
+    uint32_t s = 0;
+    JP_CUDA_TRY(cudaMemcpyAsync(&s, ctx->d_status, sizeof(s), cudaMemcpyDeviceToHost, ctx->stream));
+    JP_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (s & jp::ST_TIMEOUT) throw jp::Error{JP_ETIMEOUT, "a bounded device wait ran out"};
+    if (s & jp::ST_OVERFLOW) throw jp::Error{JP_EOVERFLOW, "a device capacity check failed"};
+    if (s & jp::ST_BADINDEX) throw jp::Error{JP_EOVERFLOW, "a device index check failed"};
+}
+
+}  // namespace
+
+extern "C" {
+
+int jp_create(jp_ctx** out, int device, void* stream, jp_alloc_fn alloc, jp_free_fn release,
+              void* user) {
+    if (!out) return JP_EINVAL;
+    *out = nullptr;
+    if ((alloc == nullptr) != (release == nullptr)) return JP_EINVAL;
+    jp_ctx* ctx = new (std::nothrow) jp_ctx();
+    if (!ctx) return JP_ENOMEM;
+    try {
+        int ndev = 0;
+        JP_CUDA_TRY(cudaGetDeviceCount(&ndev));
+        if (device < 0 || device >= ndev) throw jp::Error{JP_EINVAL, "no such device"};
+        cudaDeviceProp prop;
+        JP_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+        if (!(prop.major == 10 && prop.minor == 3))
+            throw jp::Error{JP_EUNSUPPORTED, "device is not compute capability 10.3 (sm_103)"};
+        JP_CUDA_TRY(cudaSetDevice(device));
+        ctx->device = device;
+        ctx->stream = (cudaStream_t)stream;
+        ctx->ws.alloc = alloc;
+        ctx->ws.release = release;
+        ctx->ws.user = user;
+        ctx->ws.stream = ctx->stream;
+        JP_CUDA_TRY(cudaHostAlloc((void**)&ctx->hist_host, 2048 * sizeof(uint32_t), cudaHostAllocDefault));
+        JP_CUDA_TRY(cudaHostAlloc((void**)&ctx->host_scalars, 64 * sizeof(int64_t), cudaHostAllocDefault));
+        JP_CUDA_TRY(cudaMalloc((void**)&ctx->d_status, 256));
+        for (int i = 0; i < jp::TM_SLOTS; ++i) {
+            JP_CUDA_TRY(cudaEventCreate(&ctx->tm.b[i]));
+            JP_CUDA_TRY(cudaEventCreate(&ctx->tm.e[i]));
+        }
+        std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+    } catch (const jp::Error& e) {
+        int code = e.code;
+        jp_destroy(ctx);
+        return code;
+    }
+    *out = ctx;
+    return JP_OK;
+}
+
+void jp_destroy(jp_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+    ctx->ws.release_all();
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->hist_host) cudaFreeHost(ctx->hist_host);
+    if (ctx->host_scalars) cudaFreeHost(ctx->host_scalars);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    for (int i = 0; i < jp::TM_SLOTS; ++i) {
+        if (ctx->tm.b[i]) cudaEventDestroy(ctx->tm.b[i]);
+        if (ctx->tm.e[i]) cudaEventDestroy(ctx->tm.e[i]);
+    }
+    cudaGetLastError();
+    delete ctx;
+}
+
+int jp_set_threshold(jp_ctx* ctx, int mode, int64_t delta1, int64_t delta2) {
+    if (!ctx) return JP_EINVAL;
+    if (mode != JP_FIXED && mode != JP_CLOSED_FORM && mode != JP_COST_MODEL)
+        return fail(ctx, JP_EINVAL, "unknown threshold mode");
+    if (mode == JP_FIXED && (delta1 < 1 || delta2 < 1))
+        return fail(ctx, JP_EINVAL, "thresholds must be >= 1");
+    ctx->mode = mode;
+    ctx->d1 = delta1;
+    ctx->d2 = delta2;
+    return JP_OK;
+}
+
+int jp_set_stream(jp_ctx* ctx, void* stream) {
+    if (!ctx) return JP_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->ws.stream = ctx->stream;
+    return JP_OK;
+}
+
+int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
+    if (!ctx) return JP_EINVAL;
+    if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->k = 2;
+    int rc = check_rel(ctx, R, "R");
+    if (rc) return rc;
+    if (S && (rc = check_rel(ctx, S, "S"))) return rc;
+    if (S && R->n + S->n >= ((int64_t)1 << 31)) return fail(ctx, JP_EUNSUPPORTED, "R and S together hold 2^31 or more tuples");
+    const auto t_start = std::chrono::steady_clock::now();
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = ctx->stream;
+        ctx->ws.reset();
+        const int64_t launches0 = jp::g_launches;
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
+        for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
+        ctx->tm.st = st;
+        jp::g_timer = &ctx->tm;
+        ctx->tm.begin(jp::TM_TOTAL);
+        jp_rel Rd = to_device(ctx, R);
+        jp_rel Sd;
+        if (S) Sd = to_device(ctx, S);
+        const bool self = (S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n);
+
+        jp::Graph g;
+        ctx->tm.begin(jp::TM_BUILD);
+        jp::build_graph(&Rd, self ? nullptr : &Sd, g, ctx->ws, st, ctx->d_status, ctx->hist_host,
+                        ctx->host_scalars);
+        ctx->tm.end(jp::TM_BUILD);
+
+        jp::Partition p;
+        double out_est = 0;
+        ctx->tm.begin(jp::TM_SELECT);
+        jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st);
+        ctx->tm.end(jp::TM_SELECT);
+        ctx->tm.begin(jp::TM_PARTITION);
+        jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
+        ctx->tm.end(jp::TM_PARTITION);
+
+        jp::Heavy h;
+        ctx->tm.begin(jp::TM_PACK);
+        jp::heavy_pack(g, p, h, ctx->ws, st);
+        ctx->tm.end(jp::TM_PACK);
+        jp::heavy_gemm(h, p, ctx->d_status, st, nullptr);
+
+        jp::LightResult lr;
+        jp::light_and_union(g, p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars);
+
+        int64_t* out_off = ctx->ws.get<int64_t>(g.nx + 1);
+        ctx->tm.begin(jp::TM_COUNT);
+        const int64_t count = jp::output_count(g, lr, out_off, ctx->ws, st, ctx->host_scalars);
+        ctx->tm.end(jp::TM_COUNT);
+        status_check(ctx);
+        if (count > 0) {
+            block_bytes = (size_t)count * 2 * sizeof(int32_t) + 512;
+            block = ctx->ws.raw_alloc(block_bytes);
+            if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
+            int32_t* ox = reinterpret_cast<int32_t*>(block);
+            int32_t* oz = reinterpret_cast<int32_t*>(
+                reinterpret_cast<char*>(block) + (((size_t)count * sizeof(int32_t) + 255) & ~(size_t)255));
+            ctx->tm.begin(jp::TM_PLACE);
+            jp::output_write(g, lr, out_off, count, ox, oz, st);
+            ctx->tm.end(jp::TM_PLACE);
+            out->col[0] = ox;
+            out->col[1] = oz;
+        }
+        ctx->tm.end(jp::TM_TOTAL);
+        status_check(ctx);
+        jp::g_timer = nullptr;
+        out->count = count;
+        out->_block = block;
+        out->_bytes = block_bytes;
+
+        jp_stats& s = ctx->stats;
+        std::memset(&s, 0, sizeof(s));
+        s.n_r = g.nr;
+        s.n_s = g.ns;
+        s.dom_x = g.nx;
+        s.dom_y = g.ny;
+        s.dom_z = g.nz;
+        s.out_join = g.out_join;
+        s.out_estimate = out_est;
+        s.delta1 = p.d1;
+        s.delta2 = p.d2;
+        s.threshold_mode = ctx->mode;
+        s.u = p.u;
+        s.v = p.v;
+        s.w = p.w;
+        s.light_candidates = lr.candidates;
+        s.out_count = count;
+        s.kernel_launches = jp::g_launches - launches0;
+        for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
+        s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        ctx->have_stats = true;
+        ctx->err.clear();
+        return JP_OK;
+    } catch (const jp::Error& e) {
+        jp::g_timer = nullptr;
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, e.code, e.msg);
+    } catch (const std::bad_alloc&) {
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, JP_ENOMEM, "host allocation failed");
+    }
+}
+
+int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
+    if (!ctx) return JP_EINVAL;
+    if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    if (k < 2 || k > 8) return fail(ctx, JP_EINVAL, "k must be in [2, 8]");
+    if (!rels) return fail(ctx, JP_EINVAL, "rels is NULL");
+    for (int i = 0; i < k; ++i) {
+        int rc = check_rel(ctx, &rels[i], "rels[i]");
+        if (rc) return rc;
+    }
+    return fail(ctx, JP_EUNSUPPORTED, "the star query path is not part of this build");
+}
+
+int jp_get_stats(const jp_ctx* ctx, jp_stats* stats) {
+    if (!ctx || !stats) return JP_EINVAL;
+    *stats = ctx->stats;
+    return ctx->have_stats ? JP_OK : JP_EINVAL;
+}
+
+int jp_result_to_host(jp_ctx* ctx, const jp_result* res, int32_t* const* host_cols) {
+    if (!ctx || !res || (!host_cols && res->count > 0)) return JP_EINVAL;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        for (int i = 0; i < res->k && res->count > 0; ++i) {
+            if (!host_cols[i] || !res->col[i]) return fail(ctx, JP_EINVAL, "NULL column");
+            JP_CUDA_TRY(cudaMemcpyAsync(host_cols[i], res->col[i], (size_t)res->count * sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        JP_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    } catch (const jp::Error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return JP_OK;
+}
+
+void jp_result_free(jp_ctx* ctx, jp_result* res) {
+    if (!ctx || !res) return;
+    if (res->_block) ctx->ws.raw_free(res->_block, res->_bytes);
+    std::memset(res, 0, sizeof(*res));
+}
+
+const char* jp_last_error(const jp_ctx* ctx) {
+    if (!ctx) return "NULL context";
+    return ctx->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,364 @@
+// Heavy part: matrix construction and the Boolean matrix product
+// (Section 2.2 "Join-Project as Matrix Multiplication"; Algorithm 1,
+// "M1 <- R^+ adj matrix, M2 <- S^+ adj matrix, M <- M1 x M2").
+//
+// M1 (heavy x by heavy y) and M2^T (heavy z by heavy y) are stored as dense
+// 0/1 byte matrices, K-major (the heavy y index is contiguous), with the byte
+// values 0x00 and 0x38, which are 0.0 and 1.0 in FP8 E4M3.  The product runs
+// on the 5th-generation tensor cores as tcgen05.mma.kind::f8f6f4 with FP32
+// accumulation in tensor memory: every product term is 0 or 1 and every sum
+// is a count of witnesses y, which FP32 holds exactly up to 2^24 (and a sum
+// of non-negative terms is never rounded to zero, so the test "M_ac > 0" is
+// exact at any size).  The epilogue reads each 128 x 256 accumulator tile
+// from tensor memory and stores one bit per entry, M_ac > 0, into a row-major
+// bitmap G (heavy x by heavy z); the count matrix never reaches HBM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "jp_internal.cuh"
+
+namespace jp {
+namespace {
+
+constexpr int BM = 128;           // rows of A per tile (heavy x)
+constexpr int BN = 256;           // rows of B per tile (heavy z)
+constexpr int BK = 128;           // bytes (= FP8 elements) of K per stage
+constexpr int STAGES = 4;
+constexpr int A_STAGE = BM * BK;  // 16 KB
+constexpr int B_STAGE = BN * BK;  // 32 KB
+constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
+constexpr int GEMM_THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM, warps 2..5: epilogue
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per bounded wait
+constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+// Instruction descriptor of tcgen05.mma kind::f8f6f4: D = F32 (bits 4-5 = 1),
+// A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the status word gets ST_TIMEOUT) after WAIT_NS.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > WAIT_NS) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major with the 128-byte swizzle that the
+// TMA loads produce: start address >> 4 (bits 0-13), leading byte offset 1
+// (unused by swizzled K-major layouts, bits 16-29), stride byte offset
+// 1024 B between 8-row groups (bits 32-45), descriptor version 1 (bits
+// 46-47), layout SWIZZLE_128B = 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// One 128 x 256 output tile per CTA.  K is consumed in BK-byte stages through
+// a STAGES-deep TMA ring; each stage feeds BK/32 MMAs (K = 32 per FP8 MMA).
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    heavy_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB, int num_kb, uint32_t* __restrict__ G,
+                      int64_t g_stride, uint32_t* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accum = empty + STAGES;
+    uint64_t* drain = accum + 1;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM;
+    const int n0 = blockIdx.x * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < num_kb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u, status)) break;
+            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(sA + s * A_STAGE, &tmA, &full[s], kb * BK, m0);
+            tma_load_2d(sB + s * B_STAGE, &tmB, &full[s], kb * BK, n0);
+            ++issued;
+        }
+        // drain: every issued load has landed before the CTA may exit
+        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+            mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, status);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        bool ok = true;
+        int kb = 0;
+        for (; kb < num_kb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph, status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + s * A_STAGE);
+            const uint32_t b0 = smem_u32(sB + s * B_STAGE);
+#pragma unroll
+            for (int k = 0; k < BK / 32; ++k) {
+                mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC,
+                       (kb | k) != 0 ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(accum);
+        // wait for every issued MMA before teardown (bounded)
+        mma_commit(drain);
+        mbar_wait(drain, 0, status);
+        (void)ok;
+    } else if (warp >= 2) {
+        // ---------------- epilogue: TMEM -> bits -> G
+        const int q = warp & 3;                // TMEM lane quadrant of this warp
+        const int row = m0 + q * 32 + lane;
+        if (mbar_wait(accum, 0, status)) {
+            tc_fence_after();
+            uint32_t* grow = G + (int64_t)row * g_stride + (n0 >> 5);
+#pragma unroll 1
+            for (int j = 0; j < BN / 32; ++j) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
+                uint32_t bits = 0;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) bits |= (r[i] != 0u ? 1u : 0u) << i;
+                grow[j] = bits;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------- matrix build
+__global__ void pack_rows_kernel(const int32_t* row_inv, int64_t nrows, const int32_t* off,
+                                 const int32_t* col, const int32_t* col_map, uint8_t* M,
+                                 int64_t ld) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = warp; h < nrows; h += nwarps) {
+        int32_t a = row_inv[h];
+        for (int32_t e = off[a] + lane; e < off[a + 1]; e += 32) {
+            int32_t j = col_map[col[e]];
+            if (j >= 0) M[h * ld + j] = 0x38;
+        }
+    }
+}
+
+// M2^T: for heavy y column j, every heavy z in S[y] sets B[hz][j]
+__global__ void pack_cols_kernel(const int32_t* col_inv, int64_t ncols, const int32_t* off,
+                                 const int32_t* rows, const int32_t* row_map, uint8_t* M,
+                                 int64_t ld) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp; j < ncols; j += nwarps) {
+        int32_t b = col_inv[j];
+        for (int32_t e = off[b] + lane; e < off[b + 1]; e += 32) {
+            int32_t l = row_map[rows[e]];
+            if (l >= 0) M[(int64_t)l * ld + j] = 0x38;
+        }
+    }
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        JP_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                      cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !p)
+            throw Error{JP_ECUDA, "cuTensorMapEncodeTiled is not available"};
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+CUtensorMap make_map(const uint8_t* base, int64_t rows, int64_t k_bytes, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)k_bytes, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)k_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void*)base, dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{JP_ECUDA, "cuTensorMapEncodeTiled failed"};
+    return m;
+}
+
+}  // namespace
+
+void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStream_t st) {
+    h.present = (p.u > 0 && p.v > 0 && p.w > 0);
+    if (!h.present) return;
+    h.u_pad = round_up(p.u, BM);
+    h.w_pad = round_up(p.w, BN);
+    h.v_pad = round_up(p.v, BK);
+    h.g_stride = h.w_pad / 32;
+    h.A = reinterpret_cast<uint8_t*>(ws.carve((size_t)(h.u_pad * h.v_pad)));
+    h.B = reinterpret_cast<uint8_t*>(ws.carve((size_t)(h.w_pad * h.v_pad)));
+    h.G = ws.get<uint32_t>((size_t)(h.u_pad * h.g_stride));
+    JP_CUDA_TRY(cudaMemsetAsync(h.A, 0, (size_t)(h.u_pad * h.v_pad), st));
+    JP_CUDA_TRY(cudaMemsetAsync(h.B, 0, (size_t)(h.w_pad * h.v_pad), st));
+    pack_rows_kernel<<<grid_for(p.u * 32, 256, 152 * 16), 256, 0, st>>>(
+        p.hx_inv, p.u, g.rxoff, g.rycol, p.hy, h.A, h.v_pad);
+    JP_CHECK_LAUNCH();
+    pack_cols_kernel<<<grid_for(p.v * 32, 256, 152 * 16), 256, 0, st>>>(
+        p.hy_inv, p.v, g.syoff, g.szcol, p.hz, h.B, h.v_pad);
+    JP_CHECK_LAUNCH();
+}
+
+void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
+                void* (*)()) {
+    (void)p;
+    if (!h.present) return;
+    CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
+    CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
+    static bool attr = false;
+    if (!attr) {
+        JP_CUDA_TRY(cudaFuncSetAttribute(heavy_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GEMM_SMEM));
+        attr = true;
+    }
+    dim3 grid((unsigned)(h.w_pad / BN), (unsigned)(h.u_pad / BM));
+    tbegin(TM_GEMM);
+    heavy_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(ma, mb, (int)(h.v_pad / BK), h.G,
+                                                              h.g_stride, d_status);
+    JP_CHECK_LAUNCH();
+    tend(TM_GEMM);
+}
+
+}  // namespace jp

@@ -1,0 +1,188 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/jp.h"
+
+namespace jp {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define JP_CUDA_TRY(expr)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            throw ::jp::Error{JP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// Every kernel launch of the library is followed by JP_CHECK_LAUNCH, which
+// also counts it (reported per query in jp_stats.kernel_launches).
+extern int64_t g_launches;
+#define JP_CHECK_LAUNCH()                 \
+    do {                                  \
+        ++::jp::g_launches;               \
+        JP_CUDA_TRY(cudaGetLastError());  \
+    } while (0)
+
+// Device status word bits (set by kernels; read by the host at sync points).
+enum : uint32_t {
+    ST_OVERFLOW = 1u << 0,   // a capacity check failed and the write was skipped
+    ST_TIMEOUT = 1u << 1,    // a bounded wait ran out
+    ST_BADINDEX = 1u << 2,   // an index check failed (should never happen)
+};
+
+// ---------------------------------------------------------------- memory
+// Workspace: chunks obtained through the context's allocator, carved by a
+// bump pointer that is reset at the start of every query and reused.
+struct Arena {
+    struct Chunk { char* p; size_t size; };
+    std::vector<Chunk> chunks;
+    size_t cur = 0;      // chunk index
+    size_t off = 0;      // offset in chunk
+    jp_alloc_fn alloc = nullptr;
+    jp_free_fn release = nullptr;
+    void* user = nullptr;
+    cudaStream_t stream = nullptr;
+    size_t peak = 0, used = 0;
+
+    void reset() { cur = 0; off = 0; used = 0; }
+    void* raw_alloc(size_t bytes);
+    void raw_free(void* p, size_t bytes);
+    void* carve(size_t bytes);
+    void release_all();
+    template <class T> T* get(size_t count) {
+        return reinterpret_cast<T*>(carve(count * sizeof(T) + 16));
+    }
+};
+
+// ---------------------------------------------------------------- primitives
+// Exclusive scan of n values into out (may alias in); writes the total to
+// *d_total if non-null (device pointer).
+void scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* d_total, Arena& ws,
+              cudaStream_t st);
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* d_total, Arena& ws,
+              cudaStream_t st);
+
+// LSD radix sort of uint64 keys.  Sorts keys[0..n) (using tmp as the ping-pong
+// buffer) and returns whichever of the two buffers holds the sorted keys.
+// Byte passes whose digit is constant over all keys are skipped; this needs
+// one host synchronisation (the 8x256 digit histogram).  The buffer pair
+// hist_host (pinned, >= 2048 entries) receives the histogram.
+uint64_t* radix_sort_u64(uint64_t* keys, uint64_t* tmp, int64_t n, Arena& ws, cudaStream_t st,
+                         uint32_t* hist_host);
+
+// Compact the distinct entries of sorted keys into out; count to *d_count.
+void unique_u64(const uint64_t* keys, int64_t n, uint64_t* out, uint32_t* d_count, Arena& ws,
+                cudaStream_t st);
+
+// ---------------------------------------------------------------- pipeline state
+// Normalised relations in dense ids.  All arrays are device memory.
+struct Graph {
+    bool self = true;
+    int64_t nr = 0, ns = 0;        // distinct tuples of R (after dropping dangling) and S
+    int64_t nx = 0, ny = 0, nz = 0;
+    int32_t* xval = nullptr;       // [nx] x id -> value
+    int32_t* zval = nullptr;       // [nz] z id -> value (== xval for self-join)
+    int32_t* yval = nullptr;       // [ny]
+    int32_t* rxoff = nullptr;      // [nx+1] CSR of R by x
+    int32_t* rycol = nullptr;      // [nr] y ids, sorted within a row
+    int32_t* syoff = nullptr;      // [ny+1] CSR of S by y
+    int32_t* szcol = nullptr;      // [ns] z ids, sorted within a row
+    int32_t* deg_rx = nullptr;     // [nx]
+    int32_t* deg_ry = nullptr;     // [ny]
+    int32_t* deg_sy = nullptr;     // [ny]
+    int32_t* deg_sz = nullptr;     // [nz]
+    double out_join = 0;
+};
+
+struct Partition {
+    int64_t d1 = 1, d2 = 1;
+    int64_t u = 0, v = 0, w = 0;
+    int32_t* hx = nullptr;      // [nx] heavy x index or -1
+    int32_t* hy = nullptr;      // [ny]
+    int32_t* hz = nullptr;      // [nz]
+    int32_t* hx_inv = nullptr;  // [u]
+    int32_t* hy_inv = nullptr;  // [v]
+    int32_t* hz_inv = nullptr;  // [w]
+    int32_t* sloff = nullptr;   // [v+1] light-z lists of heavy y (S^- restricted to heavy y)
+    int32_t* slcol = nullptr;
+};
+
+struct Heavy {
+    int64_t u_pad = 0, v_pad = 0, w_pad = 0;
+    uint8_t* A = nullptr;       // [u_pad][v_pad] 0x00 / 0x38 (FP8 E4M3 0.0 / 1.0)
+    uint8_t* B = nullptr;       // [w_pad][v_pad]
+    uint32_t* G = nullptr;      // [u_pad][g_stride] bit (h,c) = product (h,c) > 0
+    int64_t g_stride = 0;       // words per row
+    bool present = false;
+};
+
+// Builders (jp_build.cu)
+void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStream_t st,
+                 uint32_t* d_status, uint32_t* hist_host, int64_t* host_scalars);
+
+// Threshold selection (jp_select.cu)
+double out_estimate(double dom_x, double out_join, double N);
+void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
+                       int64_t* d2, double* out_est, Arena& ws, cudaStream_t st);
+
+// Partition (jp_partition.cu)
+void build_partition(const Graph& g, Partition& p, Arena& ws, cudaStream_t st,
+                     int64_t* host_scalars);
+
+// Heavy part (jp_gemm.cu)
+void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStream_t st);
+void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
+                void* (*get_encode)());
+
+// Light part + union (jp_light.cu)
+struct LightResult {
+    int64_t* tmp_off = nullptr;   // [nx]
+    int32_t* cnt = nullptr;       // [nx]
+    int32_t* tmp = nullptr;
+    int64_t tmp_cap = 0;
+    int64_t candidates = 0;
+};
+void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightResult& lr,
+                     Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars);
+
+// Output (jp_output.cu)
+int64_t output_count(const Graph& g, const LightResult& lr, int64_t* out_off, Arena& ws,
+                     cudaStream_t st, int64_t* host_scalars);
+void output_write(const Graph& g, const LightResult& lr, const int64_t* out_off, int64_t count,
+                  int32_t* out_x, int32_t* out_z, cudaStream_t st);
+
+// Small helpers
+int grid_for(int64_t n, int block, int max_blocks = 152 * 32);
+
+// Per-query device timing with CUDA events on the query stream, one
+// begin/end pair per pass or kernel (reported in jp_stats.ms_pass).
+enum TimerSlot {
+    TM_BUILD = 0, TM_SELECT, TM_PARTITION, TM_PACK, TM_GEMM, TM_CLASSIFY, TM_LIGHT_WARP,
+    TM_LIGHT_C2, TM_LIGHT_C16, TM_LIGHT_BITMAP, TM_COUNT, TM_PLACE, TM_TOTAL, TM_SLOTS = 16
+};
+struct Timer {
+    cudaEvent_t b[TM_SLOTS] = {}, e[TM_SLOTS] = {};
+    bool used[TM_SLOTS] = {};
+    cudaStream_t st = nullptr;
+    void begin(int k) { cudaEventRecord(b[k], st); used[k] = true; }
+    void end(int k) { cudaEventRecord(e[k], st); }
+    float ms(int k) const {
+        float v = 0;
+        if (used[k] && cudaEventElapsedTime(&v, b[k], e[k]) != cudaSuccess) { cudaGetLastError(); v = 0; }
+        return v;
+    }
+};
+extern Timer* g_timer;
+inline void tbegin(int k) { if (g_timer) g_timer->begin(k); }
+inline void tend(int k) { if (g_timer) g_timer->end(k); }
+
+}  // namespace jp

@@ -1,0 +1,256 @@
+// Threshold selection (Section 3.1 closed forms, Section 5 cost-based
+// optimizer, Algorithm 3).
+//
+// The degree indexes of Section 5 are built on the device as exact degree
+// histograms: values with degree <= HMAX are counted per degree, the few with
+// larger degree are listed individually.  The host then answers every index
+// query of Algorithm 3 exactly:
+//   sum(y_d)   = sum over light y (deg <= d) of deg_R(y) * deg_S(y)
+//                (the light-y join size; deg^2 for a self-join)
+//   sum(x_d)   = sum over light x of sum_{b in R[x]} deg_S(b)
+//                (the deduplication effort of light x)
+//   cdfx(y_d)  = sum over light y of deg_R(y)
+//   count(w_d) = number of values of w with degree <= d
+// The y degree used for y is max(deg_R(y), deg_S(y)) (the partition rule).
+#include <algorithm>
+#include <cmath>
+
+#include "jp_internal.cuh"
+
+namespace jp {
+namespace {
+
+constexpr int HMAX = 4096;
+
+struct DevHist {
+    unsigned long long x_cnt[HMAX + 1];
+    unsigned long long x_cand[HMAX + 1];
+    unsigned long long y_cnt[HMAX + 1];
+    unsigned long long y_w[HMAX + 1];
+    unsigned long long y_r[HMAX + 1];
+    unsigned long long z_cnt[HMAX + 1];
+    unsigned int n_xo, n_yo, n_zo;
+};
+
+struct Over { long long deg; unsigned long long a, b; };
+
+__global__ void hist_x_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
+                              const int32_t* deg_sy, DevHist* H, Over* xo) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = warp; a < nx; a += nwarps) {
+        unsigned long long c = 0;
+        for (int32_t e = rxoff[a] + lane; e < rxoff[a + 1]; e += 32) c += deg_sy[rycol[e]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+            const int32_t d = rxoff[a + 1] - rxoff[a];
+            if (d <= HMAX) {
+                atomicAdd(&H->x_cnt[d], 1ull);
+                atomicAdd(&H->x_cand[d], c);
+            } else {
+                unsigned int i = atomicAdd(&H->n_xo, 1u);
+                xo[i] = Over{d, c, 0};
+            }
+        }
+    }
+}
+
+__global__ void hist_y_kernel(int64_t ny, const int32_t* deg_ry, const int32_t* deg_sy,
+                              DevHist* H, Over* yo) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ny;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const long long r = deg_ry[b], s = deg_sy[b];
+        const long long d = r > s ? r : s;
+        const unsigned long long wgt = (unsigned long long)(r * s);
+        if (d <= HMAX) {
+            atomicAdd(&H->y_cnt[d], 1ull);
+            atomicAdd(&H->y_w[d], wgt);
+            atomicAdd(&H->y_r[d], (unsigned long long)r);
+        } else {
+            unsigned int i = atomicAdd(&H->n_yo, 1u);
+            yo[i] = Over{d, wgt, (unsigned long long)r};
+        }
+    }
+}
+
+__global__ void hist_z_kernel(int64_t nz, const int32_t* deg_sz, DevHist* H, Over* zo) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nz;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const long long d = deg_sz[c];
+        if (d <= HMAX) {
+            atomicAdd(&H->z_cnt[d], 1ull);
+        } else {
+            unsigned int i = atomicAdd(&H->n_zo, 1u);
+            zo[i] = Over{d, 0, 0};
+        }
+    }
+}
+
+// Cumulative index over degrees: values with degree <= delta.
+struct Index {
+    std::vector<double> cnt, s1, s2;     // prefix over exact bins 0..HMAX
+    std::vector<long long> od;           // overflow degrees, sorted
+    std::vector<double> oc, o1, o2;      // prefix over overflow entries
+    double total_cnt = 0;
+
+    void build(const unsigned long long* c, const unsigned long long* a,
+               const unsigned long long* b, std::vector<Over> over) {
+        cnt.assign(HMAX + 2, 0);
+        s1.assign(HMAX + 2, 0);
+        s2.assign(HMAX + 2, 0);
+        for (int d = 0; d <= HMAX; ++d) {
+            cnt[d + 1] = cnt[d] + (double)c[d];
+            s1[d + 1] = s1[d] + (a ? (double)a[d] : 0.0);
+            s2[d + 1] = s2[d] + (b ? (double)b[d] : 0.0);
+        }
+        std::sort(over.begin(), over.end(), [](const Over& p, const Over& q) { return p.deg < q.deg; });
+        od.clear();
+        oc.assign(over.size() + 1, 0);
+        o1.assign(over.size() + 1, 0);
+        o2.assign(over.size() + 1, 0);
+        for (size_t i = 0; i < over.size(); ++i) {
+            od.push_back(over[i].deg);
+            oc[i + 1] = oc[i] + 1;
+            o1[i + 1] = o1[i] + (double)over[i].a;
+            o2[i + 1] = o2[i] + (double)over[i].b;
+        }
+        total_cnt = cnt[HMAX + 1] + oc[over.size()];
+    }
+    // sums over values with degree <= delta; which = 0 count, 1 first, 2 second
+    double le(double delta, int which) const {
+        const std::vector<double>& P = which == 0 ? cnt : (which == 1 ? s1 : s2);
+        const std::vector<double>& O = which == 0 ? oc : (which == 1 ? o1 : o2);
+        const long long d = (long long)std::floor(delta);
+        if (d < 0) return 0;
+        if (d <= HMAX) return P[d + 1];
+        size_t k = std::upper_bound(od.begin(), od.end(), d) - od.begin();
+        return P[HMAX + 1] + O[k];
+    }
+    double gt_count(double delta) const { return total_cnt - le(delta, 0); }
+};
+
+int64_t clamp_delta(double d, int64_t N) {
+    if (!(d >= 1.0)) return 1;
+    double f = std::floor(d);
+    if (f > (double)N) return N > 0 ? N : 1;
+    return (int64_t)f;
+}
+
+}  // namespace
+
+// Calibration constants of the GPU cost model (seconds), in the roles of
+// Table 2: T_I per light candidate inserted into a deduplication structure,
+// T_m per matrix element / per-x structure set up, T_s per sequential step of
+// the paper's scan of the light-y list for every x (0 here: the GPU
+// expansion walks each x's own neighbour list), and the product time model
+// M_hat(u,v,w) = 2uvw / mm_rate + mm_fixed.
+struct CostConsts {
+    double T_I = 1.0 / 150e9;
+    double T_m = 1.0 / 3.0e12;
+    double T_s = 0.0;
+    double mm_rate = 3.0e15;
+    double mm_fixed = 20e-6;
+    double eps = 0.05;
+    double wcoj_factor = 20.0;
+};
+
+double out_estimate(double dom_x, double out_join, double N) {
+    if (N <= 0) return 0;
+    double lo = std::max(dom_x, (out_join / N) * (out_join / N));
+    double hi = std::min(dom_x * dom_x, out_join);
+    return std::sqrt(lo * hi);
+}
+
+void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
+                       int64_t* d2, double* out_est, Arena& ws, cudaStream_t st) {
+    const int64_t N = std::max<int64_t>(std::max(g.nr, g.ns), 1);
+    *out_est = out_estimate((double)g.nx, g.out_join, (double)g.nr);
+    if (mode == JP_FIXED) {
+        *d1 = std::min<int64_t>(std::max<int64_t>(fd1, 1), N);
+        *d2 = std::min<int64_t>(std::max<int64_t>(fd2, 1), N);
+        return;
+    }
+    if (mode == JP_CLOSED_FORM) {
+        const double OUT = std::max(*out_est, 1.0);
+        const double n = (double)N;
+        double a, b;
+        if (OUT <= n) {
+            a = std::cbrt(OUT);
+            b = n / std::pow(OUT, 2.0 / 3.0);
+        } else {
+            a = b = std::cbrt(2.0 * n * n / (n + OUT));
+        }
+        *d1 = clamp_delta(a, N);
+        *d2 = clamp_delta(b, N);
+        return;
+    }
+    if (mode != JP_COST_MODEL) throw Error{JP_EINVAL, "unknown threshold mode"};
+    // ---- Algorithm 3 on exact degree indexes
+    const CostConsts K;
+    if (g.out_join <= K.wcoj_factor * (double)N) {  // plain worst-case optimal join
+        *d1 = N;
+        *d2 = N;
+        return;
+    }
+    DevHist* H = ws.get<DevHist>(1);
+    Over* xo = ws.get<Over>(g.nx + 1);
+    Over* yo = ws.get<Over>(g.ny + 1);
+    Over* zo = ws.get<Over>(g.nz + 1);
+    JP_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(DevHist), st));
+    if (g.nx) {
+        hist_x_kernel<<<grid_for(g.nx * 32, 256, 152 * 16), 256, 0, st>>>(g.nx, g.rxoff, g.rycol,
+                                                                        g.deg_sy, H, xo);
+        JP_CHECK_LAUNCH();
+    }
+    if (g.ny) {
+        hist_y_kernel<<<grid_for(g.ny, 256, 152 * 16), 256, 0, st>>>(g.ny, g.deg_ry, g.deg_sy, H, yo);
+        JP_CHECK_LAUNCH();
+    }
+    if (!g.self && g.nz) {
+        hist_z_kernel<<<grid_for(g.nz, 256, 152 * 16), 256, 0, st>>>(g.nz, g.deg_sz, H, zo);
+        JP_CHECK_LAUNCH();
+    }
+    std::vector<DevHist> hh(1);
+    JP_CUDA_TRY(cudaMemcpyAsync(hh.data(), H, sizeof(DevHist), cudaMemcpyDeviceToHost, st));
+    JP_CUDA_TRY(cudaStreamSynchronize(st));
+    const DevHist& h = hh[0];
+    std::vector<Over> vx(h.n_xo), vy(h.n_yo), vz(h.n_zo);
+    if (h.n_xo) JP_CUDA_TRY(cudaMemcpy(vx.data(), xo, h.n_xo * sizeof(Over), cudaMemcpyDeviceToHost));
+    if (h.n_yo) JP_CUDA_TRY(cudaMemcpy(vy.data(), yo, h.n_yo * sizeof(Over), cudaMemcpyDeviceToHost));
+    if (h.n_zo) JP_CUDA_TRY(cudaMemcpy(vz.data(), zo, h.n_zo * sizeof(Over), cudaMemcpyDeviceToHost));
+    Index IX, IY, IZ;
+    IX.build(h.x_cnt, h.x_cand, nullptr, vx);
+    IY.build(h.y_cnt, h.y_w, h.y_r, vy);
+    if (g.self) IZ = IX; else IZ.build(h.z_cnt, nullptr, nullptr, vz);
+
+    const double OUT = std::max(*out_est, 1.0);
+    const double n = (double)N;
+    const double dom_x = (double)g.nx;
+    auto cost = [&](double a, double b) {
+        double light = K.T_I * IY.le(a, 1) + K.T_I * IX.le(b, 1) + K.T_m * dom_x +
+                       K.T_s * IY.le(a, 2) * dom_x;
+        double u = IX.gt_count(b), v = IY.gt_count(a), w = IZ.gt_count(b);
+        double heavy = 0;
+        if (u > 0 && v > 0 && w > 0)
+            heavy = 2.0 * u * v * w / K.mm_rate + K.mm_fixed + K.T_m * (u * v + u * w);
+        return light + heavy;
+    };
+    double a = n, b = std::max(n * a / OUT, 1.0);
+    double prev_cost = INFINITY, pa = a, pb = b;
+    for (int it = 0; it < 100000; ++it) {
+        double c = cost(a, b);
+        if (c > prev_cost) break;
+        prev_cost = c;
+        pa = a;
+        pb = b;
+        if (a <= 1.0) break;
+        a = std::max(a * (1.0 - K.eps), 1.0);
+        b = std::max(n * a / OUT, 1.0);
+    }
+    *d1 = clamp_delta(pa, N);
+    *d2 = clamp_delta(pb, N);
+}
+
+}  // namespace jp

@@ -1,0 +1,230 @@
+"""Python binding of the C-ABI library ``libjp.so`` (argument marshalling only).
+
+Every step of the query runs in the library's CUDA kernels; this module only
+converts torch tensors to pointers, hands PyTorch's caching allocator to the
+library, and wraps the result columns as torch tensors without copying.
+
+There is no fallback: if ``libjp.so`` is missing, or no sm_103 GPU is
+present, the calls raise.
+
+Functions mirror the C names: ``jp_two_path`` -> ``Context.two_path``,
+``jp_star`` -> ``Context.star``, ``jp_set_threshold`` ->
+``Context.set_threshold``, ``jp_get_stats`` -> ``Context.stats``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libjp.so")
+
+JP_OK, JP_EINVAL, JP_ENOMEM, JP_ECUDA, JP_EOVERFLOW, JP_ETIMEOUT, JP_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+JP_FIXED, JP_CLOSED_FORM, JP_COST_MODEL = 0, 1, 2
+_MODES = {"fixed": JP_FIXED, "closed_form": JP_CLOSED_FORM, "cost_model": JP_COST_MODEL}
+_CODES = {JP_EINVAL: "JP_EINVAL", JP_ENOMEM: "JP_ENOMEM", JP_ECUDA: "JP_ECUDA",
+          JP_EOVERFLOW: "JP_EOVERFLOW", JP_ETIMEOUT: "JP_ETIMEOUT",
+          JP_EUNSUPPORTED: "JP_EUNSUPPORTED"}
+
+
+class JPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class jp_rel(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class jp_result(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_void_p * 8), ("count", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("_block", ctypes.c_void_p), ("_bytes", ctypes.c_size_t)]
+
+
+class jp_stats(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int64), ("n_s", ctypes.c_int64), ("dom_x", ctypes.c_int64),
+                ("dom_y", ctypes.c_int64), ("dom_z", ctypes.c_int64),
+                ("out_join", ctypes.c_double), ("out_estimate", ctypes.c_double),
+                ("delta1", ctypes.c_int64), ("delta2", ctypes.c_int64),
+                ("threshold_mode", ctypes.c_int32), ("u", ctypes.c_int64),
+                ("v", ctypes.c_int64), ("w", ctypes.c_int64),
+                ("light_candidates", ctypes.c_int64), ("out_count", ctypes.c_int64),
+                ("heavy_pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("ms_total", ctypes.c_double),
+                ("ms_pass", ctypes.c_double * 16)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libjp.so; raises if it has not been built."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with "
+                                   "python -m paper_2002_12459_gb300.build")
+            lib = ctypes.CDLL(path)
+            vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            lib.jp_create.argtypes = [ctypes.POINTER(vp), i32, vp, ALLOC_FN, FREE_FN, vp]
+            lib.jp_create.restype = i32
+            lib.jp_destroy.argtypes = [vp]
+            lib.jp_destroy.restype = None
+            lib.jp_set_threshold.argtypes = [vp, i32, i64, i64]
+            lib.jp_set_threshold.restype = i32
+            lib.jp_set_stream.argtypes = [vp, vp]
+            lib.jp_set_stream.restype = i32
+            lib.jp_two_path.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
+                                        ctypes.POINTER(jp_result)]
+            lib.jp_two_path.restype = i32
+            lib.jp_star.argtypes = [vp, i32, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
+            lib.jp_star.restype = i32
+            lib.jp_get_stats.argtypes = [vp, ctypes.POINTER(jp_stats)]
+            lib.jp_get_stats.restype = i32
+            lib.jp_result_to_host.argtypes = [vp, ctypes.POINTER(jp_result),
+                                              ctypes.POINTER(ctypes.c_void_p)]
+            lib.jp_result_to_host.restype = i32
+            lib.jp_result_free.argtypes = [vp, ctypes.POINTER(jp_result)]
+            lib.jp_result_free.restype = None
+            lib.jp_last_error.argtypes = [vp]
+            lib.jp_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _rel_of(x, y) -> jp_rel:
+    import torch
+    for t in (x, y):
+        if t.dtype != torch.int32 or not t.is_contiguous():
+            raise TypeError("relation columns must be contiguous int32 tensors")
+    if x.numel() != y.numel():
+        raise ValueError("relation columns differ in length")
+    return jp_rel(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), x.numel())
+
+
+class Context:
+    """One jp_ctx on one CUDA device, issuing work on one stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._live = {}
+
+        def _alloc(nbytes, _stream, _user):
+            try:
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+            except RuntimeError:
+                return None
+            p = t.data_ptr()
+            self._live[p] = t
+            return p
+
+        def _free(ptr, _nbytes, _stream, _user):
+            self._live.pop(ptr, None)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            rc = self.lib.jp_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
+                                    self._alloc_cb, self._free_cb, None)
+        if rc != JP_OK:
+            raise JPError(rc, "jp_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            with self._torch.cuda.stream(self.stream):
+                self.lib.jp_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != JP_OK:
+            raise JPError(rc, self.lib.jp_last_error(self.h).decode())
+
+    def set_threshold(self, mode="closed_form", delta1: int = 1, delta2: int = 1):
+        m = _MODES[mode] if isinstance(mode, str) else int(mode)
+        self._check(self.lib.jp_set_threshold(self.h, m, int(delta1), int(delta2)))
+
+    def _take(self, res: jp_result):
+        """Wrap result columns as int32 tensors viewing the library's block."""
+        torch = self._torch
+        k, n = res.k, res.count
+        if n == 0:
+            self.lib.jp_result_free(self.h, ctypes.byref(res))
+            return tuple(torch.empty(0, dtype=torch.int32, device=self.device) for _ in range(k))
+        blk = self._live.get(res._block)
+        if blk is None:
+            raise RuntimeError("result block was not allocated through this context")
+        cols = []
+        for i in range(k):
+            off = res.col[i] - res._block
+            cols.append(blk[off:off + 4 * n].view(torch.int32))
+        self.lib.jp_result_free(self.h, ctypes.byref(res))   # the views keep the storage
+        return tuple(cols)
+
+    def two_path(self, rx, ry, sz=None, sy=None):
+        """Sorted distinct (x, z) of Q(x,z) = R(x,y), S(z,y); S defaults to R."""
+        R = _rel_of(rx, ry)
+        S = _rel_of(sz, sy) if sz is not None else None
+        res = jp_result()
+        with self._torch.cuda.stream(self.stream):
+            rc = self.lib.jp_two_path(self.h, ctypes.byref(R), ctypes.byref(S) if S else None,
+                                      ctypes.byref(res))
+        self._check(rc)
+        return self._take(res)
+
+    def star(self, rels):
+        """Sorted distinct k-tuples of Q*_k over ``rels = [(x1, y1), ...]``."""
+        k = len(rels)
+        arr = (jp_rel * k)(*[_rel_of(x, y) for x, y in rels])
+        res = jp_result()
+        with self._torch.cuda.stream(self.stream):
+            rc = self.lib.jp_star(self.h, k, arr, ctypes.byref(res))
+        self._check(rc)
+        return self._take(res)
+
+    def two_path_host(self, rx, ry, out_cols=None):
+        """End-to-end call with HOST input columns (pinned torch CPU tensors).
+
+        The library copies the inputs to the device; the result is copied
+        back into pinned host tensors with jp_result_to_host.
+        """
+        torch = self._torch
+        R = _rel_of(rx, ry)
+        res = jp_result()
+        with torch.cuda.stream(self.stream):
+            self._check(self.lib.jp_two_path(self.h, ctypes.byref(R), None, ctypes.byref(res)))
+        n = res.count
+        if out_cols is None or out_cols[0].numel() < n:
+            out_cols = [torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        ptrs = (ctypes.c_void_p * 2)(out_cols[0].data_ptr(), out_cols[1].data_ptr())
+        try:
+            self._check(self.lib.jp_result_to_host(self.h, ctypes.byref(res), ptrs))
+        finally:
+            self.lib.jp_result_free(self.h, ctypes.byref(res))
+        return out_cols[0][:n], out_cols[1][:n]
+
+    def stats(self) -> dict:
+        s = jp_stats()
+        self._check(self.lib.jp_get_stats(self.h, ctypes.byref(s)))
+        d = {name: getattr(s, name) for name, _ in jp_stats._fields_ if name != "ms_pass"}
+        d["ms_pass"] = list(s.ms_pass)
+        return d

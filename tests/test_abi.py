@@ -1,0 +1,56 @@
+"""The C-ABI library loads and exports every symbol include/jp.h declares.
+
+No compute call is made: this runs without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "jp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(jp_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(n for n in names if not n.endswith("_fn")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_12459_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("jp_two_path", "jp_star", "jp_set_threshold", "jp_create", "jp_destroy",
+              "jp_get_stats", "jp_result_free", "jp_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    lib.jp_two_path.restype = ctypes.c_int
+    lib.jp_two_path.argtypes = [ctypes.c_void_p] * 4
+    assert lib.jp_two_path(None, None, None, None) == -1          # JP_EINVAL
+    lib.jp_set_threshold.restype = ctypes.c_int
+    lib.jp_set_threshold.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64]
+    assert lib.jp_set_threshold(None, 0, 1, 1) == -1
+    lib.jp_last_error.restype = ctypes.c_char_p
+    lib.jp_last_error.argtypes = [ctypes.c_void_p]
+    assert lib.jp_last_error(None) == b"NULL context"
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2002_12459_gb300 import jp
+    monkeypatch.setattr(jp, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        jp.load(str(tmp_path / "missing.so"))

@@ -1,0 +1,162 @@
+"""Parity of the CUDA two-path path (through the C-ABI) with the CPU oracle.
+
+The result is a set of integer pairs, so the bar is bit-exact equality of
+the sorted distinct pairs and of their count.  Inputs are seeded and
+synthetic; thresholds are swept because Algorithm 1's output must not depend
+on them (the correctness argument after Algorithm 1).
+"""
+import numpy as np
+import pytest
+
+from paper_2002_12459_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2002_12459_gb300 import build, jp
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the -m gpu tests")
+    c = jp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def run(ctx, rx, ry, sz=None, sy=None, mode="fixed", d1=1, d2=1):
+    ctx.set_threshold(mode, d1, d2)
+    if sz is None:
+        ox, oz = ctx.two_path(dev(rx), dev(ry))
+    else:
+        ox, oz = ctx.two_path(dev(rx), dev(ry), dev(sz), dev(sy))
+    return ox.cpu().numpy(), oz.cpu().numpy()
+
+
+def assert_same(got, want):
+    gx, gz = got
+    wx, wz = want
+    assert len(gx) == len(wx), (len(gx), len(wx))
+    assert np.array_equal(gx, wx)
+    assert np.array_equal(gz, wz)
+
+
+def rand_rel(rng, n, dx, dy, ox=0, oy=0, skew=0.0):
+    return W.random_small_relation(rng, n, dx, dy, ox, oy, skew)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_small_self_join_threshold_sweep(ctx, oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    rx, ry = rand_rel(rng, 3000, 400, 150, -200, -70, skew=0.8)
+    want = oracle_mod.two_path(rx, ry)
+    for d1, d2 in [(1, 1), (2, 2), (3, 7), (10, 3), (25, 25), (10 ** 6, 10 ** 6), (1, 10 ** 6),
+                   (10 ** 6, 1)]:
+        assert_same(run(ctx, rx, ry, d1=d1, d2=d2), want)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_two_relations(ctx, oracle_mod, seed):
+    rng = np.random.default_rng(100 + seed)
+    rx, ry = rand_rel(rng, 2500, 300, 120, 5, -60, skew=0.7)
+    sz, sy = rand_rel(rng, 1800, 250, 150, -1000, -60, skew=0.5)
+    want = oracle_mod.two_path(rx, ry, sz, sy)
+    for d1, d2 in [(1, 1), (2, 5), (8, 8), (10 ** 6, 10 ** 6)]:
+        assert_same(run(ctx, rx, ry, sz, sy, d1=d1, d2=d2), want)
+
+
+def test_uniform_20k_fixed_sqrt_threshold(ctx, oracle_mod):
+    rx, ry = W.make("two_path_uniform_20k")
+    want = oracle_mod.two_path(rx, ry)
+    assert_same(run(ctx, rx, ry, d1=141, d2=141), want)
+    st = ctx.stats()
+    assert st["delta1"] == 141 and st["u"] == 0          # every x degree <= 23: all light
+    assert st["out_count"] == len(want[0])
+
+
+def test_uniform_20k_all_heavy(ctx, oracle_mod):
+    # thresholds 1: every x (degree >= 2) and y (degree >= 25) is heavy,
+    # so the answer comes from the tensor-core product alone
+    rx, ry = W.make("two_path_uniform_20k")
+    want = oracle_mod.two_path(rx, ry)
+    assert_same(run(ctx, rx, ry, d1=1, d2=1), want)
+    st = ctx.stats()
+    assert st["u"] == 2000 and st["v"] == 500 and st["light_candidates"] == 0
+
+
+@pytest.mark.parametrize("mode", ["closed_form", "cost_model"])
+def test_uniform_20k_model_thresholds(ctx, oracle_mod, mode):
+    rx, ry = W.make("two_path_uniform_20k")
+    want = oracle_mod.two_path(rx, ry)
+    assert_same(run(ctx, rx, ry, mode=mode), want)
+
+
+def test_complete_bipartite(ctx):
+    a, b = 700, 300
+    xs, ys = np.meshgrid(np.arange(a), np.arange(b), indexing="ij")
+    for d in (1, 100, 10 ** 6):
+        ox, oz = run(ctx, xs.ravel(), ys.ravel(), d1=d, d2=d)
+        assert len(ox) == a * a
+        assert np.array_equal(ox, np.repeat(np.arange(a), a))
+        assert np.array_equal(oz, np.tile(np.arange(a), a))
+
+
+def test_star_graph_and_duplicates(ctx):
+    d = 5000
+    xs = (np.arange(d) * 7 - 20000).astype(np.int32)
+    ys = np.full(d, -3, np.int32)
+    xs2 = np.concatenate([xs, xs[:100]])                  # duplicate tuples
+    ys2 = np.concatenate([ys, ys[:100]])
+    ox, oz = run(ctx, xs2, ys2, d1=10 ** 6, d2=10 ** 6)
+    assert len(ox) == d * d
+    srt = np.sort(xs)
+    assert np.array_equal(ox, np.repeat(srt, d)) and np.array_equal(oz, np.tile(srt, d))
+
+
+def test_empty_and_single(ctx):
+    e = np.empty(0, np.int32)
+    ox, oz = run(ctx, e, e)
+    assert len(ox) == 0
+    ox, oz = run(ctx, np.array([5], np.int32), np.array([-9], np.int32))
+    assert ox.tolist() == [5] and oz.tolist() == [5]
+    # disjoint y: R and S share no y value
+    ox, oz = run(ctx, np.array([1, 2], np.int32), np.array([3, 4], np.int32),
+                 np.array([7], np.int32), np.array([5], np.int32))
+    assert len(ox) == 0
+
+
+def test_extreme_values(ctx, oracle_mod):
+    big = np.iinfo(np.int32)
+    rx = np.array([big.min, big.max, 0, big.min, -1, big.max], np.int32)
+    ry = np.array([big.max, big.max, big.min, big.min, big.max, 0], np.int32)
+    want = oracle_mod.two_path(rx, ry)
+    for d in (1, 1000):
+        assert_same(run(ctx, rx, ry, d1=d, d2=d), want)
+
+
+def test_bitmap_window_wider_than_shared_memory(ctx, oracle_mod):
+    # 2.1M distinct x values (z domain > one 1.835M-bit window) and a few
+    # heavy x whose candidates span both windows
+    n = 2_100_000
+    base = np.arange(n, dtype=np.int32)
+    rx = np.concatenate([base, np.full(3, -1, np.int32), np.full(3, -2, np.int32)])
+    ry = np.concatenate([base % 700_000, np.array([0, 1, 699_999, 5, 6, 7], np.int32)])
+    ox, oz = run(ctx, rx, ry, d1=10 ** 6, d2=2)
+    st = ctx.stats()
+    assert st["u"] == 2
+    # rows of the heavy x and a sample of light x against the per-row oracle
+    srt = oracle_mod.SortedS(rx, ry)
+    starts = np.searchsorted(ox, [-2, -1, 0, 12345, 2_000_001], side="left")
+    ends = np.searchsorted(ox, [-2, -1, 0, 12345, 2_000_001], side="right")
+    for a, s, e in zip([-2, -1, 0, 12345, 2_000_001], starts, ends):
+        want = oracle_mod.two_path_row(ry[rx == a], srt)
+        assert np.array_equal(oz[s:e], want)
+    # each base x shares its y with two others (3 pairs); the 18 base x on the
+    # six special y gain the special x; each special x reaches 3 * 3 + 1 z
+    assert len(ox) == 3 * n + 18 + 2 * 10
