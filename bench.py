@@ -1,0 +1,369 @@
+"""Benchmark of the two-path join-project query on GB300.
+
+One step = one ``jp_two_path`` call through the C-ABI on device-resident
+inputs: index build, threshold selection (Algorithm 3 by default),
+partition, heavy matrices + tensor-core product, light expansion and
+deduplication, union and output placement, ending with the sorted distinct
+(x, z) columns in HBM.  The workload is the 10M-tuple power-law relation
+(x: 2M values, degree exponent 2.1; y: 1M values, exponent 1.8), self-join.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (bounded samples of the same workload).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "two-path/star query ms & distinct tuples/s, learned vs cost-model Δ, bit-exact"
+UNIT = "distinct tuples/s"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ----------------------------------------------------------------- workload
+def make_workload(name):
+    from paper_2002_12459_gb300 import workloads as W
+    t = time.time()
+    rx, ry = W.make(name)
+    log(f"[bench] workload {name}: {len(rx)} tuples drawn in {time.time() - t:.1f}s")
+    return rx, ry, W.WORKLOADS[name]
+
+
+def candidate_counts(rx, ry):
+    """Per distinct x (sorted): number of join candidates sum_{y in R[x]} deg(y)."""
+    key = np.unique((rx.astype(np.int64) << 32) | (ry.astype(np.int64) & 0xFFFFFFFF))
+    x = (key >> 32).astype(np.int64)
+    y = (key & 0xFFFFFFFF).astype(np.int64)
+    uy, yi, cy = np.unique(y, return_inverse=True, return_counts=True)
+    ux, xi = np.unique(x, return_inverse=True)
+    cand = np.bincount(xi, weights=cy[yi].astype(np.float64), minlength=len(ux))
+    return ux, cand
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s, p in zip(sm, power) if p > 0.25 * max(power)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle baseline
+def cpu_sample(rx, ry, target_cand):
+    """Prefix of x values whose join candidates add up to about target_cand."""
+    ux, cand = candidate_counts(rx, ry)
+    cum = np.cumsum(cand)
+    k = int(np.searchsorted(cum, target_cand)) + 1
+    k = max(1, min(k, len(ux)))
+    return int(ux[0]), int(ux[k - 1]), k, float(cum[k - 1]), len(ux), float(cum[-1])
+
+
+def run_oracle_sample(rx, ry, lo, hi):
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    ox, oz = oracle.two_path(rx, ry, x_lo=lo, x_hi=hi)
+    return len(ox), time.perf_counter() - t
+
+
+def cpu_baseline(rx, ry, target_cand=3.0e7):
+    lo, hi, k, c, nx, ctot = cpu_sample(rx, ry, target_cand)
+    n, secs = run_oracle_sample(rx, ry, lo, hi)
+    return {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"x values {lo}..{hi} ({k} of {nx} x values, {c:.3g} of {ctot:.3g} join "
+                       f"candidates), single-threaded C oracle incl. its sort of R and S; "
+                       f"{n} distinct pairs in {secs:.2f}s")}
+
+
+# ----------------------------------------------------------------- roofline
+def roofline(st, peaks, peak_kind, ms_by_slot):
+    """Roofline of the slowest single kernel of the step (average over steps)."""
+    hbm = peaks["hbm_gbs"]
+    fp8_burst = 2.0 * peaks["bf16_tflops"]          # nominal fp8/bf16 dense ratio 4.5/2.25
+    names = {4: "heavy_gemm_kernel", 6: "light_warp_kernel", 7: "light_block_kernel<2048>",
+             8: "light_block_kernel<16384>", 9: "light_bitmap_kernel", 11: "place_kernel"}
+    slot = max(names, key=lambda s: ms_by_slot.get(s, 0.0))
+    ms = ms_by_slot[slot]
+    out = st["out_count"]
+    if slot == 4:
+        flops = 2.0 * st["u"] * st["v"] * st["w"]
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"kernel": names[slot], "bound": "tensor", "achieved": ach, "peak": fp8_burst,
+                "unit": "TFLOP/s", "frac": ach / fp8_burst, "traffic": None,
+                "peak_source": f"{peak_kind} bf16 burst x 2 (fp8 nominal ratio)"}
+    if slot == 11:
+        byts = 16.0 * out + 20.0 * st["dom_x"]
+    else:
+        q = slot - 6
+        byts = 4.0 * st["light_cand"][q] + 4.0 * (st["light_x"][q] + st["light_deg"][q])
+        # distinct values written by the class are not reported separately:
+        # bound them by the candidates of the class (exact only for the light x)
+        byts += 4.0 * min(st["light_cand"][q], out)
+    ach = byts / (ms * 1e-3) / 1e9
+    return {"kernel": names[slot], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": None, "peak_source": f"{peak_kind} hbm copy"}
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2002_12459_gb300 import build, jp
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    rx, ry, wl = make_workload(args.workload)
+    dx = torch.from_numpy(rx).cuda()
+    dy = torch.from_numpy(ry).cuda()
+    ctx = jp.Context(local_rank)
+    ctx.set_threshold(args.mode, args.delta1, args.delta2)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        ox, oz = ctx.two_path(dx, dy)
+        del ox, oz
+        torch.cuda.synchronize()
+        log(f"[bench] warmup {i}: {ctx.stats()['ms_pass'][12]:.2f} ms")
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms, stats, slot_ms = [], [], {}
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                     # evict L2 (256 MiB > 129 MB)
+        torch.cuda.synchronize()
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
+        ox, oz = ctx.two_path(dx, dy)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        st = ctx.stats()
+        step_ms.append(ms)
+        stats.append(st)
+        for k, v in enumerate(st["ms_pass"]):
+            slot_ms[k] = slot_ms.get(k, 0.0) + v / args.steps
+        if i < args.steps - 1:
+            del ox, oz
+        log(f"[bench] step {i}: {ms:.2f} ms, OUT={st['out_count']}, launches={st['kernel_launches']}")
+    clocks = sampler.stop()
+    st = stats[-1]
+    out = st["out_count"]
+    mean_ms = sum(step_ms) / len(step_ms)
+    t = torch.tensor([mean_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+
+    # sampled bit-exact check of the last result against the per-row oracle
+    parity = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        srt = oracle.SortedS(rx, ry)
+        hx = ox.cpu().numpy()
+        hz = oz.cpu().numpy()
+        ux = np.unique(rx)
+        rng = np.random.default_rng(0)
+        ux_c, cand = candidate_counts(rx, ry)
+        sample = list(rng.choice(ux, 24, replace=False)) + list(ux_c[np.argsort(-cand)[:4]])
+        ok = True
+        for a in sample:
+            s, e = np.searchsorted(hx, a, "left"), np.searchsorted(hx, a, "right")
+            want = oracle.two_path_row(ry[rx == a], srt)
+            ok &= bool(np.array_equal(hz[s:e], want))
+        parity = {"rows_checked": len(sample), "bit_exact": ok}
+        del hx, hz
+    del ox, oz
+
+    # end to end through the C-ABI with host buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        hrx = torch.from_numpy(rx).pin_memory()
+        hry = torch.from_numpy(ry).pin_memory()
+        cols = [torch.empty(out + 1, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        times = []
+        for i in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gx, gz = ctx.two_path_host(hrx, hry, cols)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+            del gx, gz
+        e2e = {"value": out / (sum(times) / len(times)), "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * len(rx)), "d2h_bytes_per_step": int(8 * out),
+               "ms_per_step": 1e3 * sum(times) / len(times)}
+
+    base = None
+    if rank == 0 and not args.no_cpu:
+        base = cpu_baseline(rx, ry)
+
+    peaks, kind = load_peaks()
+    rl = roofline(st, peaks, kind, slot_ms)
+    launches = sum(s["kernel_launches"] for s in stats)
+    ctx.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": world * out / (max_ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_tuples": wl["n"], "dom_x": wl["dom_x"],
+                   "gamma_x": wl["gamma_x"], "dom_y": wl["dom_y"], "gamma_y": wl["gamma_y"],
+                   "seed": wl["seed"], "query": "two-path self-join Q(x,z)=R(x,y),R(z,y)",
+                   "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
+                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": out,
+                   "light_candidates": st["light_candidates"], "out_join": st["out_join"],
+                   "heavy_gemm": "tcgen05 kind::f8f6f4, E4M3 0/1 operands, exact FP32 accumulate",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "256 MiB flush written before every step",
+                   "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
+        "roofline": rl, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "parity": parity,
+    }
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rx, ry, wl = make_workload(args.workload)
+    lo, hi, k, c, nx, ctot = cpu_sample(rx, ry, args.ref_cand)
+    for _ in range(args.warmup):
+        run_oracle_sample(rx, ry, lo, hi)
+    times, n = [], 0
+    for _ in range(args.steps):
+        n, secs = run_oracle_sample(rx, ry, lo, hi)
+        times.append(secs)
+    secs = sum(times) / len(times)
+    value = n / secs
+    sample = (f"x values {lo}..{hi} ({k} of {nx} x values, {c:.3g} of {ctot:.3g} join candidates) "
+              f"per step, single-threaded C oracle; {n} distinct pairs")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": args.workload, "n_tuples": wl["n"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="two_path_powerlaw_10m")
+    ap.add_argument("--mode", default="cost_model", choices=["fixed", "closed_form", "cost_model"])
+    ap.add_argument("--delta1", type=int, default=1)
+    ap.add_argument("--delta2", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-cand", type=float, default=1.5e7)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

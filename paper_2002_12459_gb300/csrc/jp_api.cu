@@ -305,6 +305,11 @@ int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
         s.light_candidates = lr.candidates;
         s.out_count = count;
         s.kernel_launches = jp::g_launches - launches0;
+        for (int q = 0; q < 4; ++q) {
+            s.light_x[q] = lr.class_x[q];
+            s.light_cand[q] = lr.class_cand[q];
+            s.light_deg[q] = lr.class_deg[q];
+        }
         for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
         s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         ctx->have_stats = true;

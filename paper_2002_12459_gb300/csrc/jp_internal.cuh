@@ -150,6 +150,9 @@ struct LightResult {
     int32_t* tmp = nullptr;
     int64_t tmp_cap = 0;
     int64_t candidates = 0;
+    int64_t class_x[4] = {0, 0, 0, 0};     // x per class: warp, 2K block, 16K block, bitmap
+    int64_t class_cand[4] = {0, 0, 0, 0};  // candidates per class
+    int64_t class_deg[4] = {0, 0, 0, 0};   // neighbour entries per class
 };
 void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightResult& lr,
                      Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars);

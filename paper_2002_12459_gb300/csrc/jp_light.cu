@@ -41,6 +41,8 @@ struct Counters {
     unsigned long long need;          // scratch needed
     unsigned long long candidates;    // light join size
     uint32_t q[NQ];
+    unsigned long long q_cand[NQ];    // candidates per class
+    unsigned long long q_deg[NQ];     // neighbour-list entries read per class
 };
 
 __device__ __forceinline__ uint32_t next_pow2(uint32_t v) {
@@ -89,6 +91,8 @@ __global__ void classify_kernel(int64_t nx, const int32_t* rxoff, const int32_t*
             if (q >= 0) {
                 uint32_t pos = atomicAdd(&ctr->q[q], 1u);
                 queues[(int64_t)q * nx + pos] = (int32_t)a;
+                atomicAdd(&ctr->q_cand[q], c);
+                atomicAdd(&ctr->q_deg[q], (unsigned long long)(rxoff[a + 1] - rxoff[a]));
             }
             if (ub) atomicAdd(&ctr->need, ub);
             if (c) atomicAdd(&ctr->candidates, c);
@@ -441,6 +445,11 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     JP_CUDA_TRY(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     JP_CUDA_TRY(cudaStreamSynchronize(st));
     lr.candidates = (int64_t)hc.candidates;
+    for (int q = 0; q < NQ; ++q) {
+        lr.class_x[q] = hc.q[q];
+        lr.class_cand[q] = (int64_t)hc.q_cand[q];
+        lr.class_deg[q] = (int64_t)hc.q_deg[q];
+    }
     lr.tmp_cap = (int64_t)hc.need;
     lr.tmp = ws.get<int32_t>((size_t)(lr.tmp_cap + 1));
 

@@ -52,6 +52,8 @@ class jp_stats(ctypes.Structure):
                 ("v", ctypes.c_int64), ("w", ctypes.c_int64),
                 ("light_candidates", ctypes.c_int64), ("out_count", ctypes.c_int64),
                 ("heavy_pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("light_x", ctypes.c_int64 * 4), ("light_cand", ctypes.c_int64 * 4),
+                ("light_deg", ctypes.c_int64 * 4),
                 ("ms_total", ctypes.c_double),
                 ("ms_pass", ctypes.c_double * 16)]
 
@@ -225,6 +227,8 @@ class Context:
     def stats(self) -> dict:
         s = jp_stats()
         self._check(self.lib.jp_get_stats(self.h, ctypes.byref(s)))
-        d = {name: getattr(s, name) for name, _ in jp_stats._fields_ if name != "ms_pass"}
-        d["ms_pass"] = list(s.ms_pass)
+        arrays = ("ms_pass", "light_x", "light_cand", "light_deg")
+        d = {name: getattr(s, name) for name, _ in jp_stats._fields_ if name not in arrays}
+        for name in arrays:
+            d[name] = list(getattr(s, name))
         return d
