@@ -146,6 +146,42 @@ void jp_result_free(jp_ctx* ctx, jp_result* res);
 /* Message of the last failed call on this context ("" if none). */
 const char* jp_last_error(const jp_ctx* ctx);
 
+/* ---- Allocation-free two-path query (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory when they query: code that
+ * runs while a CUDA graph is being captured, services that reserve their
+ * whole device-memory budget at start-up and forbid later allocations, plain
+ * C hosts that have no allocator to hand to jp_create, and latency-bound
+ * loops that cannot afford an allocation.  It runs the jp_two_path pipeline
+ * with every scratch buffer carved from one static __device__ array of
+ * JP_NOALLOC_SCRATCH_BYTES (held by every GPU that loads the library until
+ * the process exits) and writes into the caller's buffers.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine and needs no jp_ctx.
+ *  - R, S: DEVICE pointers only (host pointers: JP_EINVAL); S == NULL means
+ *    S = R.  Each relation holds at most JP_NOALLOC_MAX_TUPLES tuples
+ *    (larger: JP_EUNSUPPORTED, checked before any work).
+ *  - mode: JP_FIXED (delta1, delta2 >= 1) or JP_CLOSED_FORM; JP_COST_MODEL
+ *    is rejected with JP_EINVAL.
+ *  - out_x, out_z: device buffers of out_cap entries each.  *out_count (a
+ *    host pointer) receives the number of result pairs; when it exceeds
+ *    out_cap nothing is written and JP_EOVERFLOW is returned, so the caller
+ *    can retry with larger buffers.  Output order and content are those of
+ *    jp_two_path.
+ *  - A query whose scratch does not fit in the array fails with
+ *    JP_EUNSUPPORTED.
+ *  - Work runs on `stream` (a cudaStream_t) on the current device; the call
+ *    returns once the result is written.  The first call on a device looks
+ *    up the array's device address with cudaGetSymbolAddress: make that
+ *    first call before any stream capture begins.
+ *  - Every call shares the array, which keeps the last call's contents; the
+ *    call itself clears whatever must start at zero.  Calls that overlap on
+ *    the GPU (from several host threads or streams) race on the array: the
+ *    caller must serialise them. */
+#define JP_NOALLOC_SCRATCH_BYTES (128u << 20)
+#define JP_NOALLOC_MAX_TUPLES    (1 << 19)
+int jp_two_path_noalloc(const jp_rel* R, const jp_rel* S, int mode, int64_t delta1,
+                        int64_t delta2, int32_t* out_x, int32_t* out_z, int64_t out_cap,
+                        int64_t* out_count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
