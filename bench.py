@@ -152,8 +152,8 @@ def roofline(st, peaks, peak_kind, ms_by_slot):
     """Roofline of the slowest single kernel of the step (average over steps)."""
     hbm = peaks["hbm_gbs"]
     fp8_burst = 2.0 * peaks["bf16_tflops"]          # nominal fp8/bf16 dense ratio 4.5/2.25
-    names = {4: "heavy_gemm_kernel", 6: "light_warp_kernel", 7: "light_block_kernel<2048>",
-             8: "light_block_kernel<16384>", 9: "light_bitmap_kernel", 11: "place_kernel"}
+    names = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>", 7: "light_warp_kernel<2048>",
+             9: "light_bitmap_kernel", 11: "place_kernel"}
     slot = max(names, key=lambda s: ms_by_slot.get(s, 0.0))
     ms = ms_by_slot[slot]
     out = st["out_count"]

@@ -137,6 +137,12 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
 // Partition (jp_partition.cu)
 void build_partition(const Graph& g, Partition& p, Arena& ws, cudaStream_t st,
                      int64_t* host_scalars);
+// h[i] = rank among values with max(deg_a, deg_b) > thr, else -1; returns the count
+int64_t heavy_ids(const int32_t* deg_a, const int32_t* deg_b, int64_t n, int64_t thr,
+                  int32_t* h, int32_t* h_inv, Arena& ws, cudaStream_t st);
+// light-z lists (z with hz < 0) of the heavy y values of a CSR by y
+void build_light_z_lists(const int32_t* syoff, const int32_t* szcol, Partition& p, Arena& ws,
+                         cudaStream_t st);
 
 // Heavy part (jp_gemm.cu)
 void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStream_t st);

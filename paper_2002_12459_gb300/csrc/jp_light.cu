@@ -13,13 +13,14 @@
 // cheapest deduplication for its size, mirroring the paper's choice between
 // a dense marker vector and append-then-sort (Section 6, "Deduplication"):
 //   c <= 256      a warp sorts the candidates in shared memory (bitonic)
-//   c <= 2048     a 256-thread block sorts them
-//   c <= 16384    a 1024-thread block sorts them
+//   c <= 2048     a warp sorts them in a larger shared-memory buffer
 //   larger, and every heavy x: a block marks z in a shared-memory bitmap
 //                 over the z domain (windowed when the domain is larger than
-//                 shared memory); heavy rows also OR in their row of the
-//                 heavy product bitmap G, which performs the union with the
-//                 matrix part.  The set bits are emitted in z order.
+//                 shared memory) with a one-bit-per-word summary, so that
+//                 emitting and clearing cost grows with the touched words,
+//                 not with the domain.  Heavy rows also OR in their row of
+//                 the heavy product bitmap G: this is the union with the
+//                 matrix part.  Set bits are emitted in z order.
 // Each x's sorted distinct list goes to a scratch buffer at an offset taken
 // by one atomic add; the output pass then places the lists in x order.
 #include "jp_internal.cuh"
@@ -28,13 +29,12 @@ namespace jp {
 namespace {
 
 constexpr int32_t KEY_PAD = 0x7fffffff;
-constexpr int W_CAP = 256;          // warp class capacity
-constexpr int C2_CAP = 2048;        // 256-thread class capacity
-constexpr int C16_CAP = 16384;      // 1024-thread class capacity
+constexpr int W_CAP = 256;            // small warp class capacity
+constexpr int W2_CAP = 2048;          // large warp class capacity
 constexpr int BM_THREADS = 1024;
-constexpr int BM_MAX_WORDS = 56 * 1024;   // 224 KB bitmap window (1,835,008 z values)
+constexpr int BM_MAX_WORDS = 54 * 1024;  // bitmap window: 216 KB + 6.75 KB summary
 
-enum { Q_WARP = 0, Q_C2 = 1, Q_C16 = 2, Q_BITMAP = 3, NQ = 4 };
+enum { Q_WARP = 0, Q_W2 = 1, Q_UNUSED = 2, Q_BITMAP = 3, NQ = 4 };
 
 struct Counters {
     unsigned long long cursor;        // scratch cursor
@@ -58,11 +58,10 @@ __device__ __forceinline__ int64_t cand_of(int32_t b, bool heavy, const int32_t*
     return deg_sy[b];
 }
 
-// Warp per x: candidate count, class, scratch requirement.
-__global__ void classify_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
-                                const int32_t* hx, const int32_t* hy, const int32_t* sloff,
-                                const int32_t* deg_sy, int64_t w, int64_t nz, int64_t* cand,
-                                int32_t* queues, Counters* ctr) {
+// Warp per x: candidate count c(x).
+__global__ void cand_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
+                            const int32_t* hx, const int32_t* hy, const int32_t* sloff,
+                            const int32_t* deg_sy, int64_t* cand) {
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -73,34 +72,85 @@ __global__ void classify_kernel(int64_t nx, const int32_t* rxoff, const int32_t*
             c += (unsigned long long)cand_of(rycol[e], heavy, hy, sloff, deg_sy);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-        if (lane == 0) {
-            cand[a] = (int64_t)c;
-            int q;
-            unsigned long long ub;
-            if (heavy || c > (unsigned long long)C16_CAP) {
+        if (lane == 0) cand[a] = (int64_t)c;
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Thread per x: class, queue slot (warp-aggregated atomics), block-aggregated sums.
+__global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
+                             const int32_t* rxoff, int64_t w, int64_t nz, int32_t* queues,
+                             Counters* ctr) {
+    __shared__ unsigned long long s_sum[2 + 2 * NQ];
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 2 + 2 * NQ; i += blockDim.x) s_sum[i] = 0;
+    __syncthreads();
+    unsigned long long need = 0, cands = 0, qc[NQ] = {0, 0, 0, 0}, qd[NQ] = {0, 0, 0, 0};
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nx;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = base + threadIdx.x;
+        int q = -1;
+        unsigned long long c = 0, ub = 0;
+        if (a < nx) {
+            const bool heavy = hx[a] >= 0;
+            c = (unsigned long long)cand[a];
+            if (heavy || c > (unsigned long long)W2_CAP) {
                 q = Q_BITMAP;
                 ub = c + (heavy ? (unsigned long long)w : 0ull);
                 if (ub > (unsigned long long)nz) ub = (unsigned long long)nz;
-            } else if (c == 0) {
-                q = -1;
-                ub = 0;
-            } else {
-                q = c <= W_CAP ? Q_WARP : (c <= C2_CAP ? Q_C2 : Q_C16);
+            } else if (c > 0) {
+                q = c <= W_CAP ? Q_WARP : Q_W2;
                 ub = c;
             }
+            need += ub;
+            cands += c;
             if (q >= 0) {
-                uint32_t pos = atomicAdd(&ctr->q[q], 1u);
-                queues[(int64_t)q * nx + pos] = (int32_t)a;
-                atomicAdd(&ctr->q_cand[q], c);
-                atomicAdd(&ctr->q_deg[q], (unsigned long long)(rxoff[a + 1] - rxoff[a]));
+                qc[q] += c;
+                qd[q] += (unsigned long long)(rxoff[a + 1] - rxoff[a]);
             }
-            if (ub) atomicAdd(&ctr->need, ub);
-            if (c) atomicAdd(&ctr->candidates, c);
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const unsigned m = __ballot_sync(0xffffffffu, q == k);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            uint32_t pos = 0;
+            if (lane == leader) pos = atomicAdd(&ctr->q[k], (uint32_t)__popc(m));
+            pos = __shfl_sync(0xffffffffu, pos, leader);
+            if (q == k) queues[(int64_t)k * nx + pos + __popc(m & ((1u << lane) - 1u))] = (int32_t)a;
+        }
+    }
+    need = warp_sum(need);
+    cands = warp_sum(cands);
+    for (int k = 0; k < NQ; ++k) {
+        qc[k] = warp_sum(qc[k]);
+        qd[k] = warp_sum(qd[k]);
+    }
+    if (lane == 0) {
+        atomicAdd(&s_sum[0], need);
+        atomicAdd(&s_sum[1], cands);
+        for (int k = 0; k < NQ; ++k) {
+            atomicAdd(&s_sum[2 + k], qc[k]);
+            atomicAdd(&s_sum[2 + NQ + k], qd[k]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_sum[0]) atomicAdd(&ctr->need, s_sum[0]);
+        if (s_sum[1]) atomicAdd(&ctr->candidates, s_sum[1]);
+        for (int k = 0; k < NQ; ++k) {
+            if (s_sum[2 + k]) atomicAdd(&ctr->q_cand[k], s_sum[2 + k]);
+            if (s_sum[2 + NQ + k]) atomicAdd(&ctr->q_deg[k], s_sum[2 + NQ + k]);
         }
     }
 }
 
-// ------------------------------------------------------------ bitonic sorts
+// ------------------------------------------------------------ bitonic sort
 __device__ __forceinline__ void cswap(int32_t* k, uint32_t i, uint32_t p, bool up) {
     int32_t a = k[i], b = k[p];
     if ((a > b) == up) {
@@ -118,17 +168,6 @@ __device__ void bitonic_warp(int32_t* k, uint32_t n) {
                 cswap(k, i, i + j, (i & size) == 0);
             }
             __syncwarp();
-        }
-}
-
-__device__ void bitonic_block(int32_t* k, uint32_t n) {
-    for (uint32_t size = 2; size <= n; size <<= 1)
-        for (uint32_t j = size >> 1; j > 0; j >>= 1) {
-            for (uint32_t t = threadIdx.x; t < n / 2; t += blockDim.x) {
-                uint32_t i = 2 * t - (t & (j - 1));
-                cswap(k, i, i + j, (i & size) == 0);
-            }
-            __syncthreads();
         }
 }
 
@@ -183,13 +222,17 @@ struct LightArgs {
     uint32_t* status;
 };
 
-// ------------------------------------------------------------ warp class
-__global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Counters* qc) {
-    __shared__ int32_t keys_all[8][W_CAP];
+// ------------------------------------------------------------ warp classes
+// One warp per light x: gather its candidates into a per-warp shared-memory
+// buffer, bitonic-sort them, and write the distinct values in order.
+template <int CAP>
+__global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Counters* qc,
+                                  int qid) {
+    extern __shared__ int32_t dyn_keys[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    int32_t* keys = keys_all[wib];
-    const uint32_t nq = qc->q[Q_WARP];
+    int32_t* keys = dyn_keys + (size_t)wib * CAP;
+    const uint32_t nq = qc->q[qid];
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t qi = warp; qi < nq; qi += nwarps) {
@@ -199,10 +242,10 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], len = A.syoff[b + 1] - s0;
             for (int32_t t = lane; t < len; t += 32)
-                if (off + t < W_CAP) keys[off + t] = A.szcol[s0 + t];
+                if (off + t < CAP) keys[off + t] = A.szcol[s0 + t];
             off += len;
         }
-        if (off > W_CAP) {  // cannot happen: the class bound is the candidate count
+        if (off > CAP) {  // cannot happen: the class bound is the candidate count
             if (lane == 0) atomicOr(A.status, ST_BADINDEX);
             continue;
         }
@@ -238,95 +281,27 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
     }
 }
 
-// ------------------------------------------------------------ block classes
-// Gather the candidates of a light x into keys[0..n); returns n.
-__device__ uint32_t gather_block(const LightArgs& A, int32_t a, int32_t* keys, uint32_t cap,
-                                 int32_t* nb_b, int32_t* nb_off, uint32_t* sw) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int32_t e0 = A.rxoff[a], deg = A.rxoff[a + 1] - e0;
-    uint32_t base = 0;
-    for (int32_t chunk = 0; chunk < deg; chunk += blockDim.x) {
-        const int32_t i = chunk + threadIdx.x;
-        int32_t b = -1;
-        uint32_t len = 0;
-        if (i < deg) {
-            b = A.rycol[e0 + i];
-            len = (uint32_t)A.deg_sy[b];
-        }
-        uint32_t tot;
-        uint32_t ex = block_exclusive<uint32_t>(len, sw, &tot);
-        nb_b[threadIdx.x] = b;
-        nb_off[threadIdx.x] = (int32_t)(base + ex);
-        __syncthreads();
-        const int32_t cnt = min((int32_t)blockDim.x, deg - chunk);
-        for (int32_t t = warp; t < cnt; t += nw) {
-            const int32_t bb = nb_b[t];
-            const int32_t s0 = A.syoff[bb], L = A.syoff[bb + 1] - s0;
-            const uint32_t dst = (uint32_t)nb_off[t];
-            for (int32_t q = lane; q < L; q += 32)
-                if (dst + q < cap) keys[dst + q] = A.szcol[s0 + q];
-        }
-        base += tot;
-        __syncthreads();
-    }
-    return base;
-}
-
-template <int CAP>
-__global__ void light_block_kernel(LightArgs A, const int32_t* queue, const Counters* qc, int qid) {
-    extern __shared__ int32_t dyn[];
-    int32_t* keys = dyn;                       // CAP
-    int32_t* nb_b = dyn + CAP;                 // blockDim
-    int32_t* nb_off = nb_b + blockDim.x;       // blockDim
-    __shared__ uint32_t sw[32];
-    __shared__ unsigned long long s_base;
-    const uint32_t nq = qc->q[qid];
-    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
-        const int32_t a = queue[qi];
-        const uint32_t n = gather_block(A, a, keys, CAP, nb_b, nb_off, sw);
-        if (n > CAP) {
-            if (threadIdx.x == 0) atomicOr(A.status, ST_BADINDEX);
-            __syncthreads();
-            continue;
-        }
-        const uint32_t sz = max(64u, next_pow2(n));
-        for (uint32_t t = n + threadIdx.x; t < sz; t += blockDim.x) keys[t] = KEY_PAD;
-        __syncthreads();
-        bitonic_block(keys, sz);
-        // distinct values: blocked ranges per thread
-        const uint32_t ipt = (n + blockDim.x - 1) / blockDim.x;
-        const uint32_t lo = min(n, threadIdx.x * ipt), hi = min(n, lo + ipt);
-        uint32_t mine = 0;
-        for (uint32_t t = lo; t < hi; ++t) mine += (t == 0 || keys[t] != keys[t - 1]);
-        uint32_t tot;
-        uint32_t ex = block_exclusive<uint32_t>(mine, sw, &tot);
-        if (threadIdx.x == 0) s_base = atomicAdd(&A.ctr->cursor, (unsigned long long)tot);
-        __syncthreads();
-        const unsigned long long base = s_base;
-        if (base + tot > (unsigned long long)A.tmp_cap) {
-            if (threadIdx.x == 0) atomicOr(A.status, ST_OVERFLOW);
-        } else {
-            uint32_t p = ex;
-            for (uint32_t t = lo; t < hi; ++t)
-                if (t == 0 || keys[t] != keys[t - 1]) A.tmp[base + p++] = keys[t];
-            if (threadIdx.x == 0) {
-                A.cnt[a] = (int32_t)tot;
-                A.tmp_off[a] = (int64_t)base;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------ bitmap class
+__device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, int32_t r) {
+    const int32_t wi = r >> 5;
+    const uint32_t old = atomicOr(&bm[wi], 1u << (r & 31));
+    if (old == 0) atomicOr(&summ[wi >> 5], 1u << (wi & 31));
+}
+
+// Persistent blocks, one x at a time.  The bitmap and its summary start at
+// zero and are cleared word by word as they are emitted.
 __global__ void __launch_bounds__(BM_THREADS, 1)
     light_bitmap_kernel(LightArgs A, const int32_t* queue, const Counters* qc, int32_t win_words) {
-    extern __shared__ uint32_t bm[];
+    extern __shared__ uint32_t smem_bm[];
+    uint32_t* bm = smem_bm;                       // win_words
+    uint32_t* summ = smem_bm + win_words;         // win_words / 32
     __shared__ uint32_t sw[32];
     __shared__ unsigned long long s_base;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t nq = qc->q[Q_BITMAP];
     const int64_t win_bits = (int64_t)win_words * 32;
+    for (int32_t i = threadIdx.x; i < win_words + win_words / 32; i += blockDim.x) smem_bm[i] = 0;
+    __syncthreads();
     for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
         const int32_t a = queue[qi];
         const int32_t h = A.hx[a];
@@ -344,8 +319,7 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
         for (int64_t z0 = 0; z0 < A.nz; z0 += win_bits) {
             const int64_t zend = min(A.nz, z0 + win_bits);
             const int32_t nwords = (int32_t)((zend - z0 + 31) >> 5);
-            for (int32_t i = threadIdx.x; i < nwords; i += blockDim.x) bm[i] = 0;
-            __syncthreads();
+            const int32_t nsumm = (nwords + 31) >> 5;
             // light candidates, one warp per neighbour b
             for (int32_t t = warp; t < deg; t += nw) {
                 const int32_t b = A.rycol[e0 + t];
@@ -361,10 +335,7 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 }
                 for (int32_t q = lane; q < L; q += 32) {
                     const int64_t z = list[q];
-                    if (z >= z0 && z < zend) {
-                        const int32_t r = (int32_t)(z - z0);
-                        atomicOr(&bm[r >> 5], 1u << (r & 31));
-                    }
+                    if (z >= z0 && z < zend) mark(bm, summ, (int32_t)(z - z0));
                 }
             }
             // heavy product row: bit l of G[h] means (a, hz_inv[l]) is an output
@@ -379,32 +350,42 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                         const int64_t l = (int64_t)i * 32 + bt;
                         if (l < A.w) {
                             const int64_t z = A.hz_inv[l];
-                            if (z >= z0 && z < zend) {
-                                const int32_t r = (int32_t)(z - z0);
-                                atomicOr(&bm[r >> 5], 1u << (r & 31));
-                            }
+                            if (z >= z0 && z < zend) mark(bm, summ, (int32_t)(z - z0));
                         }
                     }
                 }
             }
             __syncthreads();
-            // emit set bits in z order
-            const int32_t wpt = (nwords + blockDim.x - 1) / blockDim.x;
-            const int32_t lo = min(nwords, (int32_t)threadIdx.x * wpt);
-            const int32_t hi = min(nwords, lo + wpt);
+            // emit set bits in z order: blocked ranges of summary words
+            const int32_t spt = (nsumm + blockDim.x - 1) / blockDim.x;
+            const int32_t lo = min(nsumm, (int32_t)threadIdx.x * spt);
+            const int32_t hi = min(nsumm, lo + spt);
             uint32_t mine = 0;
-            for (int32_t i = lo; i < hi; ++i) mine += __popc(bm[i]);
+            for (int32_t s = lo; s < hi; ++s) {
+                uint32_t sm = summ[s];
+                while (sm) {
+                    const int j = __ffs(sm) - 1;
+                    sm &= sm - 1;
+                    mine += __popc(bm[s * 32 + j]);
+                }
+            }
             uint32_t tot;
             const uint32_t ex = block_exclusive<uint32_t>(mine, sw, &tot);
-            if (room) {
-                unsigned long long p = base + running + ex;
-                const unsigned long long lim = base + ub;
-                for (int32_t i = lo; i < hi; ++i) {
-                    uint32_t bits = bm[i];
+            unsigned long long p = base + running + ex;
+            const unsigned long long lim = base + ub;
+            for (int32_t s = lo; s < hi; ++s) {
+                uint32_t sm = summ[s];
+                summ[s] = 0;
+                while (sm) {
+                    const int j = __ffs(sm) - 1;
+                    sm &= sm - 1;
+                    const int32_t wi = s * 32 + j;
+                    uint32_t bits = bm[wi];
+                    bm[wi] = 0;
                     while (bits) {
                         const int bt = __ffs(bits) - 1;
                         bits &= bits - 1;
-                        if (p < lim) A.tmp[p] = (int32_t)(z0 + (int64_t)i * 32 + bt);
+                        if (room && p < lim) A.tmp[p] = (int32_t)(z0 + (int64_t)wi * 32 + bt);
                         ++p;
                     }
                 }
@@ -417,7 +398,6 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
             A.cnt[a] = room ? (int32_t)min(running, ub) : 0;
             A.tmp_off[a] = (int64_t)base;
         }
-        __syncthreads();
     }
 }
 
@@ -437,8 +417,11 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     Counters* ctr = ws.get<Counters>(1);
     JP_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     tbegin(TM_CLASSIFY);
-    classify_kernel<<<grid_for(nx * 32, 256, 152 * 16), 256, 0, st>>>(
-        nx, g.rxoff, g.rycol, p.hx, p.hy, p.sloff, g.deg_sy, p.w, g.nz, cand, queues, ctr);
+    cand_kernel<<<grid_for(nx * 32, 256, 152 * 16), 256, 0, st>>>(
+        nx, g.rxoff, g.rycol, p.hx, p.hy, p.sloff, g.deg_sy, cand);
+    JP_CHECK_LAUNCH();
+    queue_kernel<<<grid_for(nx, 256, 152 * 8), 256, 0, st>>>(nx, cand, p.hx, g.rxoff, p.w, g.nz,
+                                                             queues, ctr);
     JP_CHECK_LAUNCH();
     tend(TM_CLASSIFY);
     Counters hc;
@@ -477,44 +460,37 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     A.status = d_status;
 
     if (hc.q[Q_WARP]) {
+        const size_t sm = (size_t)8 * W_CAP * sizeof(int32_t);
         tbegin(TM_LIGHT_WARP);
-        light_warp_kernel<<<grid_for((int64_t)hc.q[Q_WARP] * 32, 256, 152 * 16), 256, 0, st>>>(
-            A, queues + (int64_t)Q_WARP * nx, ctr);
+        light_warp_kernel<W_CAP><<<grid_for((int64_t)hc.q[Q_WARP] * 32, 256, 152 * 16), 256, sm, st>>>(
+            A, queues + (int64_t)Q_WARP * nx, ctr, Q_WARP);
         JP_CHECK_LAUNCH();
         tend(TM_LIGHT_WARP);
     }
-    if (hc.q[Q_C2]) {
-        const size_t sm = (C2_CAP + 2 * 256) * sizeof(int32_t);
+    if (hc.q[Q_W2]) {
+        const size_t sm = (size_t)8 * W2_CAP * sizeof(int32_t);   // 64 KB: 3 blocks per SM
+        static bool attr2 = false;
+        if (!attr2) {
+            JP_CUDA_TRY(cudaFuncSetAttribute(light_warp_kernel<W2_CAP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            attr2 = true;
+        }
         tbegin(TM_LIGHT_C2);
-        light_block_kernel<C2_CAP><<<grid_for(hc.q[Q_C2], 1, 152 * 8), 256, sm, st>>>(
-            A, queues + (int64_t)Q_C2 * nx, ctr, Q_C2);
+        light_warp_kernel<W2_CAP><<<grid_for((int64_t)hc.q[Q_W2] * 32, 256, 152 * 3), 256, sm, st>>>(
+            A, queues + (int64_t)Q_W2 * nx, ctr, Q_W2);
         JP_CHECK_LAUNCH();
         tend(TM_LIGHT_C2);
-    }
-    if (hc.q[Q_C16]) {
-        const size_t sm = (C16_CAP + 2 * 1024) * sizeof(int32_t);
-        static bool attr16 = false;
-        if (!attr16) {
-            JP_CUDA_TRY(cudaFuncSetAttribute(light_block_kernel<C16_CAP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            attr16 = true;
-        }
-        tbegin(TM_LIGHT_C16);
-        light_block_kernel<C16_CAP><<<grid_for(hc.q[Q_C16], 1, 152 * 2), 1024, sm, st>>>(
-            A, queues + (int64_t)Q_C16 * nx, ctr, Q_C16);
-        JP_CHECK_LAUNCH();
-        tend(TM_LIGHT_C16);
     }
     if (hc.q[Q_BITMAP]) {
         int64_t words = (g.nz + 31) / 32;
         int32_t win = (int32_t)std::min<int64_t>(words, BM_MAX_WORDS);
-        win = (win + 31) & ~31;
-        const size_t sm = (size_t)win * sizeof(uint32_t);
+        win = (win + 1023) & ~1023;                 // whole summary words
+        const size_t sm = (size_t)(win + win / 32) * sizeof(uint32_t);
         static bool attrb = false;
         if (!attrb) {
-            JP_CUDA_TRY(cudaFuncSetAttribute(light_bitmap_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(BM_MAX_WORDS * sizeof(uint32_t))));
+            JP_CUDA_TRY(cudaFuncSetAttribute(
+                light_bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                (int)((BM_MAX_WORDS + BM_MAX_WORDS / 32) * sizeof(uint32_t))));
             attrb = true;
         }
         tbegin(TM_LIGHT_BITMAP);

@@ -21,31 +21,63 @@ __global__ void widen_kernel(const int32_t* in, int64_t n, int64_t* out) {
         out[i] = in[i];
 }
 
+constexpr int OUT_SX = 512;   // x entries staged in shared memory per tile
+
+// largest x in [lo, hi) with off[x] <= o (off non-decreasing, off[lo] <= o)
+__device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_t hi, int64_t o) {
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= o) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One tile of OUT_THREADS * OUT_VT consecutive outputs per block.  The x
+// range covering the tile is found once; when it is short its offsets are
+// staged in shared memory.  Thread t writes outputs o0 + t + k*OUT_THREADS,
+// so each store instruction of a warp covers 32 consecutive outputs.
 __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
                              const int32_t* __restrict__ xval, const int32_t* __restrict__ zval,
                              int64_t count, int32_t* __restrict__ out_x,
                              int32_t* __restrict__ out_z) {
-    const int64_t first = ((int64_t)blockIdx.x * OUT_THREADS + threadIdx.x) * OUT_VT;
-    if (first >= count) return;
-    // largest x with out_off[x] <= first
-    int64_t lo = 0, hi = nx;
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (out_off[mid] <= first) lo = mid; else hi = mid;
+    __shared__ int64_t s_off[OUT_SX + 1];
+    __shared__ int64_t s_toff[OUT_SX];
+    __shared__ int32_t s_xv[OUT_SX];
+    __shared__ int64_t s_lo, s_hi;
+    const int64_t o0 = (int64_t)blockIdx.x * OUT_THREADS * OUT_VT;
+    const int64_t o_last = min(count, o0 + (int64_t)OUT_THREADS * OUT_VT) - 1;
+    if (threadIdx.x == 0) {
+        s_lo = find_x(out_off, 0, nx, o0);
+        s_hi = find_x(out_off, s_lo, nx, o_last) + 1;
     }
-    int64_t x = lo;
-    int64_t next = (x + 1 < nx) ? out_off[x + 1] : count;
-#pragma unroll
-    for (int i = 0; i < OUT_VT; ++i) {
-        const int64_t o = first + i;
-        if (o >= count) break;
-        while (o >= next) {
-            ++x;
-            next = (x + 1 < nx) ? out_off[x + 1] : count;
+    __syncthreads();
+    const int64_t xlo = s_lo, xhi = s_hi, nxs = xhi - xlo;
+    const bool staged = nxs <= OUT_SX;
+    if (staged) {
+        for (int64_t i = threadIdx.x; i < nxs; i += OUT_THREADS) {
+            s_off[i] = out_off[xlo + i];
+            s_toff[i] = tmp_off[xlo + i];
+            s_xv[i] = xval[xlo + i];
         }
-        const int32_t z = tmp[tmp_off[x] + (o - out_off[x])];
-        out_x[o] = xval[x];
+        if (threadIdx.x == 0) s_off[nxs] = (xhi < nx) ? out_off[xhi] : count;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int k = 0; k < OUT_VT; ++k) {
+        const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
+        if (o > o_last) break;
+        int32_t z, xv;
+        if (staged) {
+            const int64_t i = find_x(s_off, 0, nxs, o);
+            z = tmp[s_toff[i] + (o - s_off[i])];
+            xv = s_xv[i];
+        } else {
+            const int64_t x = find_x(out_off, xlo, xhi, o);
+            z = tmp[tmp_off[x] + (o - out_off[x])];
+            xv = xval[x];
+        }
+        out_x[o] = xv;
         out_z[o] = zval[z];
     }
 }

@@ -85,6 +85,8 @@ __global__ void to_i32_kernel(const uint32_t* in, int64_t n, int32_t* out) {
         out[i] = (int32_t)in[i];
 }
 
+}  // namespace
+
 int64_t heavy_ids(const int32_t* deg_a, const int32_t* deg_b, int64_t n, int64_t thr,
                   int32_t* h, int32_t* h_inv, Arena& ws, cudaStream_t st) {
     if (n <= 0) return 0;
@@ -101,8 +103,6 @@ int64_t heavy_ids(const int32_t* deg_a, const int32_t* deg_b, int64_t n, int64_t
     JP_CUDA_TRY(cudaStreamSynchronize(st));
     return c;
 }
-
-}  // namespace
 
 void build_partition(const Graph& g, Partition& p, Arena& ws, cudaStream_t st,
                      int64_t* host_scalars) {
@@ -122,14 +122,18 @@ void build_partition(const Graph& g, Partition& p, Arena& ws, cudaStream_t st,
         p.hz_inv = ws.get<int32_t>(g.nz + 1);
         p.w = heavy_ids(g.deg_sz, nullptr, g.nz, p.d2, p.hz, p.hz_inv, ws, st);
     }
-    // light-z lists of heavy y
+    build_light_z_lists(g.syoff, g.szcol, p, ws, st);
+}
+
+void build_light_z_lists(const int32_t* syoff, const int32_t* szcol, Partition& p, Arena& ws,
+                         cudaStream_t st) {
     p.sloff = ws.get<int32_t>(p.v + 2);
     uint32_t* cnt = ws.get<uint32_t>(p.v + 1);
     uint32_t* off = ws.get<uint32_t>(p.v + 1);
     uint32_t* d_tot = ws.get<uint32_t>(1);
     if (p.v > 0) {
         light_z_count_kernel<<<grid_for(p.v * 32, 256, 152 * 16), 256, 0, st>>>(
-            p.hy_inv, p.v, g.syoff, g.szcol, p.hz, cnt);
+            p.hy_inv, p.v, syoff, szcol, p.hz, cnt);
         JP_CHECK_LAUNCH();
     }
     scan_u32(cnt, off, p.v, d_tot, ws, st);
@@ -139,7 +143,7 @@ void build_partition(const Graph& g, Partition& p, Arena& ws, cudaStream_t st,
     p.slcol = ws.get<int32_t>((int64_t)tot + 1);
     if (p.v > 0) {
         light_z_fill_kernel<<<grid_for(p.v * 32, 256, 152 * 16), 256, 0, st>>>(
-            p.hy_inv, p.v, g.syoff, g.szcol, p.hz, off, p.slcol);
+            p.hy_inv, p.v, syoff, szcol, p.hz, off, p.slcol);
         JP_CHECK_LAUNCH();
         to_i32_kernel<<<G(p.v), 256, 0, st>>>(off, p.v, p.sloff);
         JP_CHECK_LAUNCH();
