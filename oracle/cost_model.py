@@ -148,3 +148,18 @@ def algorithm3(idx: DegreeIndex, N: int, OUT: float, T_I: float, T_s: float, T_m
             return to_int_threshold(d1, N), to_int_threshold(d2, N), "mm"
         d1 = max(d1 * (1.0 - eps), 1.0)
         d2 = max(N * d1 / OUT, 1.0)
+
+
+def star_grid_thresholds(N: int, OUT: float, k: int = 3, steps: int = 96):
+    """Integer (Delta1, Delta2) minimising the Section 3.2 star cost (omega = 2)
+    over a log-spaced grid of [1, N] with ``steps`` intervals per axis: the
+    Section 3.2 cost has no closed form for general k and OUT."""
+    lnN = math.log(max(N, 1))
+    grid = [max(1, math.floor(math.exp(lnN * i / steps))) for i in range(steps + 1)]
+    best, arg = math.inf, (1, 1)
+    for t1 in grid:
+        for t2 in grid:
+            c = star_cost(float(N), float(OUT), float(t1), float(t2), k)
+            if c < best:
+                best, arg = c, (t1, t2)
+    return arg

@@ -168,6 +168,28 @@ int64_t output_count(const Graph& g, const LightResult& lr, int64_t* out_off, Ar
                      cudaStream_t st, int64_t* host_scalars);
 void output_write(const Graph& g, const LightResult& lr, const int64_t* out_off, int64_t count,
                   int32_t* out_x, int32_t* out_z, cudaStream_t st);
+// Same placement with one or two per-row value columns (rowval2 may be NULL):
+// output o of row r gets (rowval[r], rowval2[r], zval[list entry]).
+void output_write_rows(const Graph& g, const LightResult& lr, const int64_t* out_off,
+                       int64_t count, const int32_t* rowval, const int32_t* rowval2,
+                       int32_t* out_row, int32_t* out_row2, int32_t* out_z, cudaStream_t st);
+
+// Star query k = 3 (jp_star.cu): builds the virtual two-path instance whose
+// rows are the (x1, x2) pairs, whose neighbour lists are the shared y of each
+// pair and whose S is R3 indexed by y; row1/row2 hold each row's x1/x2 value.
+struct StarOut {
+    Graph g;
+    Partition p;
+    int32_t* row1 = nullptr;
+    int32_t* row2 = nullptr;
+    int64_t n_rel[3] = {0, 0, 0}, nx[3] = {0, 0, 0};
+    int64_t ny = 0, triples = 0, groups = 0, d1 = 1, d2 = 1;
+    double out_join = 0;   // full star join size sum_y d1(y) d2(y) d3(y)
+};
+void run_star3(const jp_rel* rels, int mode, int64_t fd1, int64_t fd2, StarOut& so, Arena& ws,
+               cudaStream_t st, uint32_t* d_status, uint32_t* hist_host);
+// Integer (Delta1, Delta2) minimising the Section 3.2 star cost on a log grid.
+void star_thresholds(int64_t N, double out_est, int k, int64_t* d1, int64_t* d2);
 
 // Small helpers
 int grid_for(int64_t n, int block, int max_blocks = 152 * 32);

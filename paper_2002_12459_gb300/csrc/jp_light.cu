@@ -32,9 +32,9 @@ constexpr int32_t KEY_PAD = 0x7fffffff;
 constexpr int W_CAP = 256;            // small warp class capacity
 constexpr int W2_CAP = 2048;          // large warp class capacity
 constexpr int BM_THREADS = 1024;
-constexpr int BM_MAX_WORDS = 54 * 1024;  // bitmap window: 216 KB + 6.75 KB summary
+constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
 
-enum { Q_WARP = 0, Q_W2 = 1, Q_UNUSED = 2, Q_BITMAP = 3, NQ = 4 };
+enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, NQ = 4 };
 
 struct Counters {
     unsigned long long cursor;        // scratch cursor
@@ -83,9 +83,13 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // Thread per x: class, queue slot (warp-aggregated atomics), block-aggregated sums.
+// A light x with a single neighbour list needs no deduplication: S[b] is
+// sorted and distinct, so the output pass reads it in place (tmp_off holds
+// -(offset in szcol) - 1) and no scratch is used.
 __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
-                             const int32_t* rxoff, int64_t w, int64_t nz, int32_t* queues,
-                             Counters* ctr) {
+                             const int32_t* rxoff, const int32_t* rycol, const int32_t* syoff,
+                             int64_t w, int64_t nz, int32_t* queues, int32_t* cnt,
+                             int64_t* tmp_off, Counters* ctr) {
     __shared__ unsigned long long s_sum[2 + 2 * NQ];
     const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 2 + 2 * NQ; i += blockDim.x) s_sum[i] = 0;
@@ -99,10 +103,14 @@ __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
         if (a < nx) {
             const bool heavy = hx[a] >= 0;
             c = (unsigned long long)cand[a];
-            if (heavy || c > (unsigned long long)W2_CAP) {
+            if (heavy || (c > (unsigned long long)W2_CAP && rxoff[a + 1] - rxoff[a] > 1)) {
                 q = Q_BITMAP;
                 ub = c + (heavy ? (unsigned long long)w : 0ull);
                 if (ub > (unsigned long long)nz) ub = (unsigned long long)nz;
+            } else if (c > 0 && rxoff[a + 1] - rxoff[a] == 1) {
+                q = Q_COPY;
+                cnt[a] = (int32_t)c;
+                tmp_off[a] = -(int64_t)syoff[rycol[rxoff[a]]] - 1;
             } else if (c > 0) {
                 q = c <= W_CAP ? Q_WARP : Q_W2;
                 ub = c;
@@ -281,6 +289,138 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
     }
 }
 
+// ------------------------------------------------------------ bucket class
+// One warp per light x with W_CAP < c <= CAP, deduplicated by an
+// order-preserving bucket sort: pass 1 counts the candidates per bucket of
+// the z domain (bucket = z * nb / nz, monotone in z), pass 2 scatters them to
+// their bucket's range, then every lane sorts and deduplicates whole buckets
+// (about 8 values each) by insertion, and the buckets are written in order.
+// Work is linear in c; no block-wide synchronisation is needed.
+template <int CAP, int NB>
+__global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Counters* qc,
+                                    int qid) {
+    extern __shared__ int32_t dyn_b[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int32_t* buf = dyn_b + (size_t)wib * (CAP + 2 * NB);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(buf + CAP);   // per-bucket count, later distinct
+    uint32_t* cur = cnt + NB;                                 // per-bucket cursor / end
+    const uint32_t nq = qc->q[qid];
+    const uint64_t nz = (uint64_t)A.nz;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int PER = NB / 32;                              // counters per lane in scans
+    for (int64_t qi = warp; qi < nq; qi += nwarps) {
+        const int32_t a = queue[qi];
+        const uint32_t n = (uint32_t)A.cand[a];
+        if (n > CAP) {  // cannot happen: the class bound is the candidate count
+            if (lane == 0) atomicOr(A.status, ST_BADINDEX);
+            continue;
+        }
+        const uint32_t nb = min((uint32_t)NB, max(32u, next_pow2((n + 7) / 8)));
+        for (uint32_t k = lane; k < NB; k += 32) cnt[k] = 0;
+        __syncwarp();
+        const int32_t e0 = A.rxoff[a], e1 = A.rxoff[a + 1];
+        for (int32_t e = e0; e < e1; ++e) {
+            const int32_t b = A.rycol[e];
+            const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
+            for (int32_t t = lane; t < L; t += 32) {
+                const uint32_t z = (uint32_t)A.szcol[s0 + t];
+                atomicAdd(&cnt[(uint32_t)(((uint64_t)z * nb) / nz)], 1u);
+            }
+        }
+        __syncwarp();
+        // exclusive scan of the counts into the cursors
+        {
+            uint32_t loc[PER], s = 0;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) { loc[i] = cnt[lane * PER + i]; s += loc[i]; }
+            uint32_t inc = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            uint32_t run = inc - s;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) { cur[lane * PER + i] = run; run += loc[i]; }
+        }
+        __syncwarp();
+        for (int32_t e = e0; e < e1; ++e) {
+            const int32_t b = A.rycol[e];
+            const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
+            for (int32_t t = lane; t < L; t += 32) {
+                const uint32_t z = (uint32_t)A.szcol[s0 + t];
+                const uint32_t p = atomicAdd(&cur[(uint32_t)(((uint64_t)z * nb) / nz)], 1u);
+                buf[p] = (int32_t)z;
+            }
+        }
+        __syncwarp();
+        // sort + deduplicate every bucket in place; cnt[k] becomes its distinct count
+        for (uint32_t k = lane; k < nb; k += 32) {
+            const uint32_t end = cur[k], beg = end - cnt[k];
+            for (uint32_t i = beg + 1; i < end; ++i) {
+                const int32_t v = buf[i];
+                uint32_t j = i;
+                while (j > beg && buf[j - 1] > v) { buf[j] = buf[j - 1]; --j; }
+                buf[j] = v;
+            }
+            uint32_t d = 0;
+            for (uint32_t i = beg; i < end; ++i)
+                if (i == beg || buf[i] != buf[i - 1]) buf[beg + d++] = buf[i];
+            cnt[k] = d;
+        }
+        __syncwarp();
+        // positions of the buckets' distinct runs in the output
+        uint32_t total;
+        {
+            uint32_t loc[PER], s = 0;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) { loc[i] = (lane * PER + i < nb) ? cnt[lane * PER + i] : 0; s += loc[i]; }
+            uint32_t inc = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            total = __shfl_sync(0xffffffffu, inc, 31);
+            uint32_t run = inc - s;
+            // cnt[k] becomes bucket k's output position (each lane rewrites
+            // only the counters it read); cur[k] keeps the bucket's end in buf
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const uint32_t k = lane * PER + i;
+                if (k < nb) {
+                    cnt[k] = run;
+                    run += loc[i];
+                }
+            }
+        }
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&A.ctr->cursor, (unsigned long long)total);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base + total > (unsigned long long)A.tmp_cap) {
+            if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
+            continue;
+        }
+        // bucket k starts in buf where bucket k-1 ended; its distinct values
+        // were compacted to that start, and their number is the gap between
+        // consecutive output positions
+        for (uint32_t k = lane; k < nb; k += 32) {
+            const uint32_t outp = cnt[k];
+            const uint32_t d = ((k + 1 < nb) ? cnt[k + 1] : total) - outp;
+            const uint32_t beg = (k == 0) ? 0u : cur[k - 1];
+            for (uint32_t i = 0; i < d; ++i) A.tmp[base + outp + i] = buf[beg + i];
+        }
+        if (lane == 0) {
+            A.cnt[a] = (int32_t)total;
+            A.tmp_off[a] = (int64_t)base;
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------ bitmap class
 __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, int32_t r) {
     const int32_t wi = r >> 5;
@@ -297,7 +437,8 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
     uint32_t* summ = smem_bm + win_words;         // win_words / 32
     __shared__ uint32_t sw[32];
     __shared__ unsigned long long s_base;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ uint32_t s_pre[BM_THREADS];     // prefix of the neighbour list lengths
+    __shared__ int32_t s_start[BM_THREADS];    // list start (negative: in slcol)
     const uint32_t nq = qc->q[Q_BITMAP];
     const int64_t win_bits = (int64_t)win_words * 32;
     for (int32_t i = threadIdx.x; i < win_words + win_words / 32; i += blockDim.x) smem_bm[i] = 0;
@@ -320,23 +461,42 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
             const int64_t zend = min(A.nz, z0 + win_bits);
             const int32_t nwords = (int32_t)((zend - z0 + 31) >> 5);
             const int32_t nsumm = (nwords + 31) >> 5;
-            // light candidates, one warp per neighbour b
-            for (int32_t t = warp; t < deg; t += nw) {
-                const int32_t b = A.rycol[e0 + t];
-                const int32_t* list;
-                int32_t L;
-                const int32_t j = heavy ? A.hy[b] : -1;
-                if (j >= 0) {
-                    list = A.slcol + A.sloff[j];
-                    L = A.sloff[j + 1] - A.sloff[j];
-                } else {
-                    list = A.szcol + A.syoff[b];
-                    L = A.syoff[b + 1] - A.syoff[b];
+            // light candidates, flattened over the whole block: neighbours are
+            // taken BM_THREADS at a time, their list lengths prefix-summed, and
+            // thread t handles flat candidates t, t + BM_THREADS, ... (adjacent
+            // threads read adjacent list entries)
+            for (int32_t c0 = 0; c0 < deg; c0 += BM_THREADS) {
+                const int32_t i = c0 + threadIdx.x;
+                int32_t start = 0, L = 0;
+                if (i < deg) {
+                    const int32_t b = A.rycol[e0 + i];
+                    const int32_t j = heavy ? A.hy[b] : -1;
+                    if (j >= 0) {          // light z of a heavy y: negative = slcol offset
+                        start = -A.sloff[j] - 1;
+                        L = A.sloff[j + 1] - A.sloff[j];
+                    } else {
+                        start = A.syoff[b];
+                        L = A.syoff[b + 1] - start;
+                    }
                 }
-                for (int32_t q = lane; q < L; q += 32) {
-                    const int64_t z = list[q];
+                uint32_t total;
+                const uint32_t ex = block_exclusive<uint32_t>((uint32_t)L, sw, &total);
+                s_pre[threadIdx.x] = ex;
+                s_start[threadIdx.x] = start;
+                __syncthreads();
+                const int32_t nn = min(BM_THREADS, deg - c0);
+                for (uint32_t f = threadIdx.x; f < total; f += BM_THREADS) {
+                    int32_t lo = 0, hi = nn;   // last k with s_pre[k] <= f
+                    while (hi - lo > 1) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (s_pre[mid] <= f) lo = mid; else hi = mid;
+                    }
+                    const int32_t st0 = s_start[lo];
+                    const uint32_t off = f - s_pre[lo];
+                    const int64_t z = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
                     if (z >= z0 && z < zend) mark(bm, summ, (int32_t)(z - z0));
                 }
+                __syncthreads();
             }
             // heavy product row: bit l of G[h] means (a, hz_inv[l]) is an output
             if (heavy && A.G) {
@@ -420,8 +580,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     cand_kernel<<<grid_for(nx * 32, 256, 152 * 16), 256, 0, st>>>(
         nx, g.rxoff, g.rycol, p.hx, p.hy, p.sloff, g.deg_sy, cand);
     JP_CHECK_LAUNCH();
-    queue_kernel<<<grid_for(nx, 256, 152 * 8), 256, 0, st>>>(nx, cand, p.hx, g.rxoff, p.w, g.nz,
-                                                             queues, ctr);
+    queue_kernel<<<grid_for(nx, 256, 152 * 8), 256, 0, st>>>(
+        nx, cand, p.hx, g.rxoff, g.rycol, g.syoff, p.w, g.nz, queues, lr.cnt, lr.tmp_off, ctr);
     JP_CHECK_LAUNCH();
     tend(TM_CLASSIFY);
     Counters hc;
@@ -468,15 +628,11 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         tend(TM_LIGHT_WARP);
     }
     if (hc.q[Q_W2]) {
-        const size_t sm = (size_t)8 * W2_CAP * sizeof(int32_t);   // 64 KB: 3 blocks per SM
-        static bool attr2 = false;
-        if (!attr2) {
-            JP_CUDA_TRY(cudaFuncSetAttribute(light_warp_kernel<W2_CAP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            attr2 = true;
-        }
+        constexpr int NB = 256;
+        // 4 warps per block, (CAP + 2 NB) ints each: 40 KB, 5 blocks per SM
+        const size_t sm = (size_t)4 * (W2_CAP + 2 * NB) * sizeof(int32_t);
         tbegin(TM_LIGHT_C2);
-        light_warp_kernel<W2_CAP><<<grid_for((int64_t)hc.q[Q_W2] * 32, 256, 152 * 3), 256, sm, st>>>(
+        light_bucket_kernel<W2_CAP, NB><<<grid_for((int64_t)hc.q[Q_W2] * 32, 128, 152 * 5), 128, sm, st>>>(
             A, queues + (int64_t)Q_W2 * nx, ctr, Q_W2);
         JP_CHECK_LAUNCH();
         tend(TM_LIGHT_C2);

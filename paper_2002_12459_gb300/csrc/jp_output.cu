@@ -36,14 +36,24 @@ __device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_
 // range covering the tile is found once; when it is short its offsets are
 // staged in shared memory.  Thread t writes outputs o0 + t + k*OUT_THREADS,
 // so each store instruction of a warp covers 32 consecutive outputs.
+// A row's list lives in the scratch buffer (tmp_off >= 0) or, for rows with a
+// single neighbour list, in place in szcol (tmp_off = -(offset) - 1).
+__device__ __forceinline__ int32_t list_at(const int32_t* tmp, const int32_t* szcol, int64_t toff,
+                                           int64_t i) {
+    return toff >= 0 ? tmp[toff + i] : szcol[-toff - 1 + i];
+}
+
 __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
-                             const int32_t* __restrict__ xval, const int32_t* __restrict__ zval,
-                             int64_t count, int32_t* __restrict__ out_x,
+                             const int32_t* __restrict__ szcol,
+                             const int32_t* __restrict__ xval, const int32_t* __restrict__ xval2,
+                             const int32_t* __restrict__ zval, int64_t count,
+                             int32_t* __restrict__ out_x, int32_t* __restrict__ out_x2,
                              int32_t* __restrict__ out_z) {
     __shared__ int64_t s_off[OUT_SX + 1];
     __shared__ int64_t s_toff[OUT_SX];
     __shared__ int32_t s_xv[OUT_SX];
+    __shared__ int32_t s_xv2[OUT_SX];
     __shared__ int64_t s_lo, s_hi;
     const int64_t o0 = (int64_t)blockIdx.x * OUT_THREADS * OUT_VT;
     const int64_t o_last = min(count, o0 + (int64_t)OUT_THREADS * OUT_VT) - 1;
@@ -59,6 +69,7 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
             s_off[i] = out_off[xlo + i];
             s_toff[i] = tmp_off[xlo + i];
             s_xv[i] = xval[xlo + i];
+            if (xval2) s_xv2[i] = xval2[xlo + i];
         }
         if (threadIdx.x == 0) s_off[nxs] = (xhi < nx) ? out_off[xhi] : count;
     }
@@ -67,17 +78,20 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
     for (int k = 0; k < OUT_VT; ++k) {
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
         if (o > o_last) break;
-        int32_t z, xv;
+        int32_t z, xv, xv2 = 0;
         if (staged) {
             const int64_t i = find_x(s_off, 0, nxs, o);
-            z = tmp[s_toff[i] + (o - s_off[i])];
+            z = list_at(tmp, szcol, s_toff[i], o - s_off[i]);
             xv = s_xv[i];
+            if (xval2) xv2 = s_xv2[i];
         } else {
             const int64_t x = find_x(out_off, xlo, xhi, o);
-            z = tmp[tmp_off[x] + (o - out_off[x])];
+            z = list_at(tmp, szcol, tmp_off[x], o - out_off[x]);
             xv = xval[x];
+            if (xval2) xv2 = xval2[x];
         }
         out_x[o] = xv;
+        if (out_x2) out_x2[o] = xv2;
         out_z[o] = zval[z];
     }
 }
@@ -103,11 +117,18 @@ int64_t output_count(const Graph& g, const LightResult& lr, int64_t* out_off, Ar
 
 void output_write(const Graph& g, const LightResult& lr, const int64_t* out_off, int64_t count,
                   int32_t* out_x, int32_t* out_z, cudaStream_t st) {
+    output_write_rows(g, lr, out_off, count, g.xval, nullptr, out_x, nullptr, out_z, st);
+}
+
+void output_write_rows(const Graph& g, const LightResult& lr, const int64_t* out_off,
+                       int64_t count, const int32_t* rowval, const int32_t* rowval2,
+                       int32_t* out_row, int32_t* out_row2, int32_t* out_z, cudaStream_t st) {
     if (count <= 0) return;
     const int64_t per_block = (int64_t)OUT_THREADS * OUT_VT;
     const int64_t blocks = (count + per_block - 1) / per_block;
     place_kernel<<<(unsigned)blocks, OUT_THREADS, 0, st>>>(out_off, g.nx, lr.tmp_off, lr.tmp,
-                                                          g.xval, g.zval, count, out_x, out_z);
+                                                          g.szcol, rowval, rowval2, g.zval, count,
+                                                          out_row, out_row2, out_z);
     JP_CHECK_LAUNCH();
 }
 

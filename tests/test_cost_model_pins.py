@@ -133,3 +133,16 @@ def test_algorithm3_wcoj_switch_and_descent():
     d1, d2, _ = CM.algorithm3(idx, N, 3e4, 1.0, 0, 0, lambda u, v, w: 0.0, out_join=oj)
     assert idx.heavy_x(d2) > 0 and idx.heavy_y(d1) > 0
     assert 1 <= d1 <= N and 1 <= d2 <= N
+
+
+def test_star_grid_minimum_reaches_the_worked_example_exponent():
+    # Section 3.2 example (k = 3, OUT = N^(3/2)): the paper's thresholds give
+    # running time N^(15/8); the grid minimum of the same cost can only be
+    # lower, and is of the same order
+    for N in (1e6, 1e8, 1e10):
+        OUT = N ** 1.5
+        d1, d2 = CM.star_grid_thresholds(int(N), OUT, 3)
+        best = CM.star_cost(N, OUT, d1, d2, 3)
+        paper = CM.star_cost(N, OUT, N ** (7 / 16), N ** (6 / 16), 3)
+        assert best <= paper * (1 + 1e-12)
+        assert 0.5 * N ** (15 / 8) <= best
