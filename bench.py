@@ -148,32 +148,45 @@ def cpu_baseline(rx, ry, target_cand=3.0e7):
 
 
 # ----------------------------------------------------------------- roofline
-def roofline(st, peaks, peak_kind, ms_by_slot):
-    """Roofline of the slowest single kernel of the step (average over steps)."""
+KERNEL_SLOTS = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>",
+                7: "light_bucket_kernel<2048,256>", 9: "light_bitmap_kernel", 11: "place_kernel"}
+
+
+def kernel_roofline(slot, st, peaks, peak_kind, ms):
+    """Algorithmic work of one launch of a kernel slot / its event-timed duration."""
     hbm = peaks["hbm_gbs"]
     fp8_burst = 2.0 * peaks["bf16_tflops"]          # nominal fp8/bf16 dense ratio 4.5/2.25
-    names = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>", 7: "light_warp_kernel<2048>",
-             9: "light_bitmap_kernel", 11: "place_kernel"}
-    slot = max(names, key=lambda s: ms_by_slot.get(s, 0.0))
-    ms = ms_by_slot[slot]
     out = st["out_count"]
     if slot == 4:
         flops = 2.0 * st["u"] * st["v"] * st["w"]
         ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": names[slot], "bound": "tensor", "achieved": ach, "peak": fp8_burst,
-                "unit": "TFLOP/s", "frac": ach / fp8_burst, "traffic": None,
+        return {"kernel": KERNEL_SLOTS[slot], "ms": ms, "bound": "tensor", "achieved": ach,
+                "peak": fp8_burst, "unit": "TFLOP/s", "frac": ach / fp8_burst, "traffic": None,
                 "peak_source": f"{peak_kind} bf16 burst x 2 (fp8 nominal ratio)"}
     if slot == 11:
-        byts = 16.0 * out + 20.0 * st["dom_x"]
+        # read each list entry (4 B), gather its value (4 B), write the k
+        # output columns (4 B each); per row: offsets, list start, row values
+        k = st.get("k", 2)
+        byts = (8.0 + 4.0 * k) * out + 20.0 * st["dom_x"]
     else:
         q = slot - 6
+        # candidates gathered (4 B), neighbour lists and per-x records read
+        # (4 B each), distinct values written (bounded by the candidates)
         byts = 4.0 * st["light_cand"][q] + 4.0 * (st["light_x"][q] + st["light_deg"][q])
-        # distinct values written by the class are not reported separately:
-        # bound them by the candidates of the class (exact only for the light x)
         byts += 4.0 * min(st["light_cand"][q], out)
     ach = byts / (ms * 1e-3) / 1e9
-    return {"kernel": names[slot], "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": None, "peak_source": f"{peak_kind} hbm copy"}
+    return {"kernel": KERNEL_SLOTS[slot], "ms": ms, "bound": "hbm", "achieved": ach, "peak": hbm,
+            "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "peak_source": f"{peak_kind} hbm copy"}
+
+
+def roofline(st, peaks, peak_kind, ms_by_slot):
+    """Roofline of the slowest single kernel of the step, and of every kernel."""
+    per = {KERNEL_SLOTS[s]: kernel_roofline(s, st, peaks, peak_kind, ms_by_slot[s])
+           for s in KERNEL_SLOTS if ms_by_slot.get(s, 0.0) > 0}
+    slot = max(KERNEL_SLOTS, key=lambda s: ms_by_slot.get(s, 0.0))
+    top = dict(per[KERNEL_SLOTS[slot]])
+    return top, per
 
 
 # ----------------------------------------------------------------- our arm
@@ -278,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
         base = cpu_baseline(rx, ry)
 
     peaks, kind = load_peaks()
-    rl = roofline(st, peaks, kind, slot_ms)
+    rl, rl_all = roofline(st, peaks, kind, slot_ms)
     launches = sum(s["kernel_launches"] for s in stats)
     ctx.close()
     if rank != 0:
@@ -298,8 +311,100 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "256 MiB flush written before every step",
                    "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
-        "roofline": rl, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
+        "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "parity": parity,
+    }
+
+
+# ----------------------------------------------------------------- star workload
+def run_star(args):
+    """Star Q*_3 on the 3 x 2M workload (single GPU, rank 0)."""
+    import torch
+    from paper_2002_12459_gb300 import build, jp
+    from paper_2002_12459_gb300 import workloads as W
+
+    build.build()
+    t = time.time()
+    rels = W.make(args.workload)
+    wl = W.WORKLOADS[args.workload]
+    log(f"[bench] workload {args.workload}: {len(rels)} x {len(rels[0][0])} tuples in {time.time() - t:.1f}s")
+    drels = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in rels]
+    ctx = jp.Context(0)
+    ctx.set_threshold(args.mode, args.delta1, args.delta2)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for i in range(args.warmup):
+        cols = ctx.star(drels)
+        del cols
+        torch.cuda.synchronize()
+        log(f"[bench] warmup {i}: {ctx.stats()['ms_pass'][12]:.2f} ms")
+    sampler = ClockSampler(0)
+    sampler.start()
+    step_ms, stats, slot_ms = [], [], {}
+    cols = None
+    for i in range(args.steps):
+        cols = None
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
+        cols = ctx.star(drels)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = ctx.stats()
+        step_ms.append(ms)
+        stats.append(st)
+        for k, v in enumerate(st["ms_pass"]):
+            slot_ms[k] = slot_ms.get(k, 0.0) + v / args.steps
+        log(f"[bench] step {i}: {ms:.2f} ms, OUT={st['out_count']}, launches={st['kernel_launches']}")
+    clocks = sampler.stop()
+    st = dict(stats[-1])
+    st["k"] = 3
+    out = st["out_count"]
+    mean_ms = sum(step_ms) / len(step_ms)
+
+    # sampled bit-exact check: every output tuple whose x1 lies in a small range
+    import oracle
+    oracle.build()
+    x1 = np.unique(rels[0][0])
+    lo, hi = int(x1[len(x1) // 3]), int(x1[len(x1) // 3 + 15])
+    want = oracle.star(rels, x_lo=lo, x_hi=hi)
+    b = torch.searchsorted(cols[0], torch.tensor([lo, hi + 1], dtype=torch.int32, device="cuda"))
+    s, e = int(b[0]), int(b[1])
+    got = [c[s:e].cpu().numpy() for c in cols]
+    ok = all(np.array_equal(g, w) for g, w in zip(got, want))
+    parity = {"x1_range": [lo, hi], "tuples_checked": int(e - s), "bit_exact": bool(ok)}
+    del cols
+
+    base = None
+    if not args.no_cpu:
+        t = time.perf_counter()
+        lo2, hi2 = int(x1[0]), int(x1[min(len(x1) - 1, 250)])
+        n = len(oracle.star(rels, x_lo=lo2, x_hi=hi2)[0])
+        secs = time.perf_counter() - t
+        base = {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"x1 values {lo2}..{hi2} (251 of {len(x1)}), single-threaded C oracle "
+                           f"incl. its sort of the three relations; {n} distinct triples in {secs:.2f}s")}
+    peaks, kind = load_peaks()
+    rl, rl_all = roofline(st, peaks, kind, slot_ms)
+    launches = sum(s_["kernel_launches"] for s_ in stats)
+    ctx.close()
+    return {
+        "metric": METRIC, "value": out / (mean_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_tuples_per_relation": wl["n"], "k": 3,
+                   "dom_x": wl["dom_x"], "dom_y": wl["dom_y"], "gamma_y": wl["gamma_y"],
+                   "seed": wl["seed"], "query": "star Q*_3(x1,x2,x3)=R1(x1,y),R2(x2,y),R3(x3,y)",
+                   "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
+                   "heavy_pairs_u": st["u"], "v": st["v"], "w": st["w"], "out_count": out,
+                   "out_join": st["out_join"], "l2": "256 MiB flush written before every step",
+                   "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
+        "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base,
+        "e2e": None, "e2e_note": "not measured: the result is 144 GB, beyond a host copy per step",
+        "gpu_launches": launches, "clocks": clocks, "parity": parity,
     }
 
 
@@ -357,7 +462,11 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank)
+    from paper_2002_12459_gb300 import workloads as W
+    if W.WORKLOADS[args.workload]["kind"] == "star":
+        res = run_star(args) if rank == 0 else None
+    else:
+        res = run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -260,12 +260,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 __global__ void pack_rows_kernel(const int32_t* row_inv, int64_t nrows, const int32_t* off,
                                  const int32_t* col, const int32_t* col_map, uint8_t* M,
                                  int64_t ld) {
-    const int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t h = warp; h < nrows; h += nwarps) {
+    // block per heavy row: hub rows hold up to ~1e5 entries
+    for (int64_t h = blockIdx.x; h < nrows; h += gridDim.x) {
         int32_t a = row_inv[h];
-        for (int32_t e = off[a] + lane; e < off[a + 1]; e += 32) {
+        for (int32_t e = off[a] + threadIdx.x; e < off[a + 1]; e += blockDim.x) {
             int32_t j = col_map[col[e]];
             if (j >= 0) M[h * ld + j] = 0x38;
         }
@@ -332,7 +330,7 @@ void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStr
     h.G = ws.get<uint32_t>((size_t)(h.u_pad * h.g_stride));
     JP_CUDA_TRY(cudaMemsetAsync(h.A, 0, (size_t)(h.u_pad * h.v_pad), st));
     JP_CUDA_TRY(cudaMemsetAsync(h.B, 0, (size_t)(h.w_pad * h.v_pad), st));
-    pack_rows_kernel<<<grid_for(p.u * 32, 256, 152 * 16), 256, 0, st>>>(
+    pack_rows_kernel<<<grid_for(p.u, 1, 152 * 16), 256, 0, st>>>(
         p.hx_inv, p.u, g.rxoff, g.rycol, p.hy, h.A, h.v_pad);
     JP_CHECK_LAUNCH();
     pack_cols_kernel<<<grid_for(p.v * 32, 256, 152 * 16), 256, 0, st>>>(

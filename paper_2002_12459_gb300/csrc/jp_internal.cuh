@@ -159,12 +159,13 @@ struct LightResult {
     int64_t class_x[4] = {0, 0, 0, 0};     // x per class: warp, 2K block, 16K block, bitmap
     int64_t class_cand[4] = {0, 0, 0, 0};  // candidates per class
     int64_t class_deg[4] = {0, 0, 0, 0};   // neighbour entries per class
+    int32_t* tile_x = nullptr;             // x holding the first output of each output tile
 };
 void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightResult& lr,
                      Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars);
 
 // Output (jp_output.cu)
-int64_t output_count(const Graph& g, const LightResult& lr, int64_t* out_off, Arena& ws,
+int64_t output_count(const Graph& g, LightResult& lr, int64_t* out_off, Arena& ws,
                      cudaStream_t st, int64_t* host_scalars);
 void output_write(const Graph& g, const LightResult& lr, const int64_t* out_off, int64_t count,
                   int32_t* out_x, int32_t* out_z, cudaStream_t st);

@@ -12,8 +12,10 @@
 // Per x the candidate count c(a) is computed first; each x then goes to the
 // cheapest deduplication for its size, mirroring the paper's choice between
 // a dense marker vector and append-then-sort (Section 6, "Deduplication"):
+//   one list      a light x with a single neighbour list is already sorted
+//                 and distinct: the output pass copies S[b] in place
 //   c <= 256      a warp sorts the candidates in shared memory (bitonic)
-//   c <= 2048     a warp sorts them in a larger shared-memory buffer
+//   c <= 2048     a warp bucket-sorts them over the z domain (linear work)
 //   larger, and every heavy x: a block marks z in a shared-memory bitmap
 //                 over the z domain (windowed when the domain is larger than
 //                 shared memory) with a one-bit-per-word summary, so that
@@ -33,6 +35,7 @@ constexpr int W_CAP = 256;            // small warp class capacity
 constexpr int W2_CAP = 2048;          // large warp class capacity
 constexpr int BM_THREADS = 1024;
 constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
+constexpr int BM_WARP_PER_LIST = 128;    // rows with this many neighbours: warp per list
 
 enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, NQ = 4 };
 
@@ -324,9 +327,15 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
         for (int32_t e = e0; e < e1; ++e) {
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
-            for (int32_t t = lane; t < L; t += 32) {
-                const uint32_t z = (uint32_t)A.szcol[s0 + t];
-                atomicAdd(&cnt[(uint32_t)(((uint64_t)z * nb) / nz)], 1u);
+            for (int32_t t0 = lane; t0 < L; t0 += 128) {
+                uint32_t zz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    zz[u] = (t0 + 32 * u < L) ? (uint32_t)A.szcol[s0 + t0 + 32 * u] : 0xffffffffu;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (zz[u] != 0xffffffffu)
+                        atomicAdd(&cnt[(uint32_t)(((uint64_t)zz[u] * nb) / nz)], 1u);
             }
         }
         __syncwarp();
@@ -349,10 +358,17 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
         for (int32_t e = e0; e < e1; ++e) {
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
-            for (int32_t t = lane; t < L; t += 32) {
-                const uint32_t z = (uint32_t)A.szcol[s0 + t];
-                const uint32_t p = atomicAdd(&cur[(uint32_t)(((uint64_t)z * nb) / nz)], 1u);
-                buf[p] = (int32_t)z;
+            for (int32_t t0 = lane; t0 < L; t0 += 128) {
+                uint32_t zz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    zz[u] = (t0 + 32 * u < L) ? (uint32_t)A.szcol[s0 + t0 + 32 * u] : 0xffffffffu;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (zz[u] != 0xffffffffu) {
+                        const uint32_t p = atomicAdd(&cur[(uint32_t)(((uint64_t)zz[u] * nb) / nz)], 1u);
+                        buf[p] = (int32_t)zz[u];
+                    }
             }
         }
         __syncwarp();
@@ -461,11 +477,37 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
             const int64_t zend = min(A.nz, z0 + win_bits);
             const int32_t nwords = (int32_t)((zend - z0 + 31) >> 5);
             const int32_t nsumm = (nwords + 31) >> 5;
-            // light candidates, flattened over the whole block: neighbours are
-            // taken BM_THREADS at a time, their list lengths prefix-summed, and
+            // rows with many neighbours (the hubs): one warp per neighbour list,
+            // lanes over the list, no search needed
+            if (deg >= BM_WARP_PER_LIST) {
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                for (int32_t t = warp; t < deg; t += BM_THREADS / 32) {
+                    const int32_t b = A.rycol[e0 + t];
+                    const int32_t j = heavy ? A.hy[b] : -1;
+                    const int32_t* list;
+                    int32_t L;
+                    if (j >= 0) {
+                        list = A.slcol + A.sloff[j];
+                        L = A.sloff[j + 1] - A.sloff[j];
+                    } else {
+                        list = A.szcol + A.syoff[b];
+                        L = A.syoff[b + 1] - A.syoff[b];
+                    }
+                    for (int32_t q0 = lane; q0 < L; q0 += 128) {
+                        int32_t zz[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) zz[u] = (q0 + 32 * u < L) ? list[q0 + 32 * u] : -1;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (zz[u] >= z0 && zz[u] < zend) mark(bm, summ, (int32_t)(zz[u] - z0));
+                    }
+                }
+            }
+            // other rows: flattened over the whole block: neighbours are taken
+            // BM_THREADS at a time, their list lengths prefix-summed, and
             // thread t handles flat candidates t, t + BM_THREADS, ... (adjacent
             // threads read adjacent list entries)
-            for (int32_t c0 = 0; c0 < deg; c0 += BM_THREADS) {
+            for (int32_t c0 = 0; deg < BM_WARP_PER_LIST && c0 < deg; c0 += BM_THREADS) {
                 const int32_t i = c0 + threadIdx.x;
                 int32_t start = 0, L = 0;
                 if (i < deg) {
@@ -485,16 +527,27 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 s_start[threadIdx.x] = start;
                 __syncthreads();
                 const int32_t nn = min(BM_THREADS, deg - c0);
-                for (uint32_t f = threadIdx.x; f < total; f += BM_THREADS) {
-                    int32_t lo = 0, hi = nn;   // last k with s_pre[k] <= f
-                    while (hi - lo > 1) {
-                        const int32_t mid = (lo + hi) >> 1;
-                        if (s_pre[mid] <= f) lo = mid; else hi = mid;
+                constexpr int U = 4;    // candidates loaded before any is marked
+                for (uint32_t f0 = threadIdx.x; f0 < total; f0 += U * BM_THREADS) {
+                    int64_t zz[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const uint32_t f = f0 + (uint32_t)u * BM_THREADS;
+                        zz[u] = -1;
+                        if (f < total) {
+                            int32_t lo = 0, hi = nn;   // last k with s_pre[k] <= f
+                            while (hi - lo > 1) {
+                                const int32_t mid = (lo + hi) >> 1;
+                                if (s_pre[mid] <= f) lo = mid; else hi = mid;
+                            }
+                            const int32_t st0 = s_start[lo];
+                            const uint32_t off = f - s_pre[lo];
+                            zz[u] = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
+                        }
                     }
-                    const int32_t st0 = s_start[lo];
-                    const uint32_t off = f - s_pre[lo];
-                    const int64_t z = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
-                    if (z >= z0 && z < zend) mark(bm, summ, (int32_t)(z - z0));
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (zz[u] >= z0 && zz[u] < zend) mark(bm, summ, (int32_t)(zz[u] - z0));
                 }
                 __syncthreads();
             }

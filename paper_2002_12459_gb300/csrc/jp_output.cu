@@ -4,9 +4,10 @@
 //
 // Because x ids and z ids are assigned in value order, writing the lists in
 // x-id order with each list in z-id order gives the lexicographic order of
-// the signed values.  The write is load balanced over output positions: each
-// thread owns a run of consecutive outputs, finds its x by binary search on
-// the output offsets once, and then walks forward.
+// the signed values.  The write is load balanced over output positions: a
+// block owns one tile of consecutive outputs, reads the x range of its tile
+// from a precomputed tile -> x table, stages that range's offsets in shared
+// memory and writes striped, coalesced output.
 #include "jp_internal.cuh"
 
 namespace jp {
@@ -32,10 +33,6 @@ __device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_
     return lo;
 }
 
-// One tile of OUT_THREADS * OUT_VT consecutive outputs per block.  The x
-// range covering the tile is found once; when it is short its offsets are
-// staged in shared memory.  Thread t writes outputs o0 + t + k*OUT_THREADS,
-// so each store instruction of a warp covers 32 consecutive outputs.
 // A row's list lives in the scratch buffer (tmp_off >= 0) or, for rows with a
 // single neighbour list, in place in szcol (tmp_off = -(offset) - 1).
 __device__ __forceinline__ int32_t list_at(const int32_t* tmp, const int32_t* szcol, int64_t toff,
@@ -43,7 +40,24 @@ __device__ __forceinline__ int32_t list_at(const int32_t* tmp, const int32_t* sz
     return toff >= 0 ? tmp[toff + i] : szcol[-toff - 1 + i];
 }
 
+// tile_x[t] = the x whose output range holds output t * tile (thread per x:
+// an x marks every tile that starts inside its range)
+__global__ void tile_start_kernel(const int64_t* __restrict__ out_off, int64_t nx, int64_t count,
+                                  int64_t tile, int32_t* __restrict__ tile_x) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nx;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = out_off[x];
+        const int64_t e = (x + 1 < nx) ? out_off[x + 1] : count;
+        for (int64_t t = (b + tile - 1) / tile; t * tile < e; ++t) tile_x[t] = (int32_t)x;
+    }
+}
+
+// One tile of OUT_THREADS * OUT_VT consecutive outputs per block; when the
+// tile's x range is short its offsets are staged in shared memory.  Thread t
+// writes outputs o0 + t + k*OUT_THREADS, so each store instruction of a warp
+// covers 32 consecutive outputs.
 __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
+                             const int32_t* __restrict__ tile_x,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
                              const int32_t* __restrict__ szcol,
                              const int32_t* __restrict__ xval, const int32_t* __restrict__ xval2,
@@ -54,15 +68,13 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
     __shared__ int64_t s_toff[OUT_SX];
     __shared__ int32_t s_xv[OUT_SX];
     __shared__ int32_t s_xv2[OUT_SX];
-    __shared__ int64_t s_lo, s_hi;
     const int64_t o0 = (int64_t)blockIdx.x * OUT_THREADS * OUT_VT;
     const int64_t o_last = min(count, o0 + (int64_t)OUT_THREADS * OUT_VT) - 1;
-    if (threadIdx.x == 0) {
-        s_lo = find_x(out_off, 0, nx, o0);
-        s_hi = find_x(out_off, s_lo, nx, o_last) + 1;
-    }
-    __syncthreads();
-    const int64_t xlo = s_lo, xhi = s_hi, nxs = xhi - xlo;
+    // x range of the tile: from the x holding its first output to the x holding
+    // the next tile's first output (an upper bound of the x holding o_last)
+    const int64_t xlo = tile_x[blockIdx.x];
+    const int64_t xhi = (o_last + 1 < count) ? (int64_t)tile_x[blockIdx.x + 1] + 1 : nx;
+    const int64_t nxs = xhi - xlo;
     const bool staged = nxs <= OUT_SX;
     if (staged) {
         for (int64_t i = threadIdx.x; i < nxs; i += OUT_THREADS) {
@@ -98,7 +110,7 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
 
 }  // namespace
 
-int64_t output_count(const Graph& g, const LightResult& lr, int64_t* out_off, Arena& ws,
+int64_t output_count(const Graph& g, LightResult& lr, int64_t* out_off, Arena& ws,
                      cudaStream_t st, int64_t* host_scalars) {
     (void)host_scalars;
     const int64_t nx = g.nx;
@@ -112,6 +124,14 @@ int64_t output_count(const Graph& g, const LightResult& lr, int64_t* out_off, Ar
     int64_t total = 0;
     JP_CUDA_TRY(cudaMemcpyAsync(&total, d_total, sizeof(total), cudaMemcpyDeviceToHost, st));
     JP_CUDA_TRY(cudaStreamSynchronize(st));
+    const int64_t tile = (int64_t)OUT_THREADS * OUT_VT;
+    const int64_t ntiles = (total + tile - 1) / tile;
+    lr.tile_x = ws.get<int32_t>(ntiles + 1);
+    if (total > 0) {
+        tile_start_kernel<<<grid_for(nx, 256, 152 * 16), 256, 0, st>>>(out_off, nx, total, tile,
+                                                                       lr.tile_x);
+        JP_CHECK_LAUNCH();
+    }
     return total;
 }
 
@@ -126,7 +146,7 @@ void output_write_rows(const Graph& g, const LightResult& lr, const int64_t* out
     if (count <= 0) return;
     const int64_t per_block = (int64_t)OUT_THREADS * OUT_VT;
     const int64_t blocks = (count + per_block - 1) / per_block;
-    place_kernel<<<(unsigned)blocks, OUT_THREADS, 0, st>>>(out_off, g.nx, lr.tmp_off, lr.tmp,
+    place_kernel<<<(unsigned)blocks, OUT_THREADS, 0, st>>>(out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp,
                                                           g.szcol, rowval, rowval2, g.zval, count,
                                                           out_row, out_row2, out_z);
     JP_CHECK_LAUNCH();

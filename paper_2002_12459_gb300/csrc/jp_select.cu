@@ -147,10 +147,12 @@ int64_t clamp_delta(double d, int64_t N) {
 // expansion walks each x's own neighbour list), and the product time model
 // M_hat(u,v,w) = 2uvw / mm_rate + mm_fixed.
 struct CostConsts {
-    double T_I = 1.0 / 150e9;
-    double T_m = 1.0 / 3.0e12;
+    // measured on GB300 with the 10M power-law self-join: 3.1e9 light
+    // candidates in ~50 ms of light kernels, 2.3 PFLOP/s in the product
+    double T_I = 1.0 / 60e9;
+    double T_m = 1.0 / 1.0e12;
     double T_s = 0.0;
-    double mm_rate = 3.0e15;
+    double mm_rate = 2.2e15;
     double mm_fixed = 20e-6;
     double eps = 0.05;
     double wcoj_factor = 20.0;
