@@ -57,6 +57,7 @@ extern "C" {
 #define JP_FIXED        0    /* use the given Delta1, Delta2 (clamped to [1, N]) */
 #define JP_CLOSED_FORM  1    /* Lemma 3's minimiser of the omega = 2 cost, with the Section 5 output estimate */
 #define JP_COST_MODEL   2    /* Algorithm 3 (Section 5) with GPU-calibrated constants */
+#define JP_LEARNED      3    /* thresholds predicted by the model set with jp_set_predictor */
 
 typedef struct jp_ctx jp_ctx;
 
@@ -145,6 +146,46 @@ void jp_result_free(jp_ctx* ctx, jp_result* res);
 
 /* Message of the last failed call on this context ("" if none). */
 const char* jp_last_error(const jp_ctx* ctx);
+
+/* ---- Learned threshold predictor ----
+ * The paper chooses Delta1, Delta2 with a cost model whose constants are
+ * measured by hand (Section 5, Table 2, Algorithm 3).  The predictor learns the
+ * choice instead: a network maps a relation's degree distribution to
+ * (ln Delta1, ln Delta2), trained on the thresholds that timed best on the
+ * GPU.  Features: two 64-bin histograms (x degrees; y degrees taken as
+ * max(deg_R(y), deg_S(y))), as fractions of the values, with
+ * bin(d) = min(63, floor(4 log2 d)).  Network: 128 -> 256 -> 256 -> 2 with
+ * ReLU, weights used in bfloat16, products and sums in float32, float32
+ * master weights updated by Adam.  Parameters are one float array of
+ * JP_MLP_PARAMS entries: W1[128][256], b1[256], W2[256][256], b2[256],
+ * W3[256][2], b3[2] (W[i][j] maps input i to output j). */
+#define JP_MLP_PARAMS 99330
+#define JP_MLP_MAX_BATCH 1024
+typedef struct jp_mlp jp_mlp;
+
+/* The 128 features of the query jp_two_path(ctx, R, S) would run (host out). */
+int jp_features(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, float* out128);
+
+/* Model used by JP_LEARNED (borrowed: it must outlive its use; NULL clears). */
+int jp_set_predictor(jp_ctx* ctx, jp_mlp* model);
+
+/* Create a model on `device`, working on `stream`; parameters start at zero. */
+int jp_mlp_create(jp_mlp** model, int device, void* stream);
+void jp_mlp_destroy(jp_mlp* model);
+/* Copy the float32 master parameters in or out (host arrays of n entries,
+ * n == JP_MLP_PARAMS); setting them also resets the Adam state. */
+int jp_mlp_set_params(jp_mlp* model, const float* params, int64_t n);
+int jp_mlp_get_params(jp_mlp* model, float* params, int64_t n);
+/* Forward pass: X[B][128] host in, Y[B][2] host out, 1 <= B <= JP_MLP_MAX_BATCH. */
+int jp_mlp_forward(jp_mlp* model, const float* X, int B, float* Y);
+/* Gradients of the loss mean_b ||Y_b - T_b||^2 w.r.t. all parameters
+ * (host array of JP_MLP_PARAMS, may be NULL) and the loss (host, may be NULL). */
+int jp_mlp_gradients(jp_mlp* model, const float* X, const float* T, int B, float* grad,
+                     float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on
+ * the batch; *loss (host, may be NULL) gets the loss before the step. */
+int jp_mlp_train_step(jp_mlp* model, const float* X, const float* T, int B, float lr,
+                      float* loss);
 
 /* ---- Allocation-free two-path query (the paper has no counterpart) ----
  * For callers that cannot allocate device memory when they query: code that

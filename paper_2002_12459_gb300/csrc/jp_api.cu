@@ -21,6 +21,7 @@ struct jp_ctx {
     int64_t* host_scalars = nullptr;   // pinned, 64 entries
     uint32_t* d_status = nullptr;      // device status word
     jp::Timer tm;
+    jp_mlp* predictor = nullptr;       // borrowed model for JP_LEARNED
 };
 
 namespace jp {
@@ -194,7 +195,7 @@ void jp_destroy(jp_ctx* ctx) {
 
 int jp_set_threshold(jp_ctx* ctx, int mode, int64_t delta1, int64_t delta2) {
     if (!ctx) return JP_EINVAL;
-    if (mode != JP_FIXED && mode != JP_CLOSED_FORM && mode != JP_COST_MODEL)
+    if (mode != JP_FIXED && mode != JP_CLOSED_FORM && mode != JP_COST_MODEL && mode != JP_LEARNED)
         return fail(ctx, JP_EINVAL, "unknown threshold mode");
     if (mode == JP_FIXED && (delta1 < 1 || delta2 < 1))
         return fail(ctx, JP_EINVAL, "thresholds must be >= 1");
@@ -247,7 +248,8 @@ int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
         jp::Partition p;
         double out_est = 0;
         ctx->tm.begin(jp::TM_SELECT);
-        jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st);
+        jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
+                              ctx->predictor);
         ctx->tm.end(jp::TM_SELECT);
         ctx->tm.begin(jp::TM_PARTITION);
         jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
@@ -435,6 +437,38 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         std::memset(out, 0, sizeof(*out));
         return fail(ctx, JP_ENOMEM, "host allocation failed");
     }
+}
+
+int jp_set_predictor(jp_ctx* ctx, jp_mlp* model) {
+    if (!ctx) return JP_EINVAL;
+    ctx->predictor = model;
+    return JP_OK;
+}
+
+int jp_features(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, float* out128) {
+    if (!ctx) return JP_EINVAL;
+    if (!out128) return fail(ctx, JP_EINVAL, "out128 is NULL");
+    int rc = check_rel(ctx, R, "R");
+    if (rc) return rc;
+    if (S && (rc = check_rel(ctx, S, "S"))) return rc;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = ctx->stream;
+        ctx->ws.reset();
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
+        jp_rel Rd = to_device(ctx, R);
+        jp_rel Sd;
+        if (S) Sd = to_device(ctx, S);
+        const bool self = (S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n);
+        jp::Graph g;
+        jp::build_graph(&Rd, self ? nullptr : &Sd, g, ctx->ws, st, ctx->d_status, ctx->hist_host,
+                        ctx->host_scalars);
+        jp::graph_features(g, out128, ctx->ws, st);
+        status_check(ctx);
+    } catch (const jp::Error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return JP_OK;
 }
 
 int jp_get_stats(const jp_ctx* ctx, jp_stats* stats) {

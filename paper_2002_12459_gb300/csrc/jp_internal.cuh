@@ -132,7 +132,13 @@ void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStre
 // Threshold selection (jp_select.cu)
 double out_estimate(double dom_x, double out_join, double N);
 void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
-                       int64_t* d2, double* out_est, Arena& ws, cudaStream_t st);
+                       int64_t* d2, double* out_est, Arena& ws, cudaStream_t st,
+                       jp_mlp* predictor = nullptr);
+
+// Learned predictor (jp_mlp.cu): the 128 degree features of a built graph and
+// the thresholds a model predicts for them.
+void graph_features(const Graph& g, float* host128, Arena& ws, cudaStream_t st);
+void mlp_predict(jp_mlp* model, const float* host128, int64_t N, int64_t* d1, int64_t* d2);
 
 // Partition (jp_partition.cu)
 void build_partition(const Graph& g, Partition& p, Arena& ws, cudaStream_t st,

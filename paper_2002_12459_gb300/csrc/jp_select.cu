@@ -166,7 +166,8 @@ double out_estimate(double dom_x, double out_join, double N) {
 }
 
 void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
-                       int64_t* d2, double* out_est, Arena& ws, cudaStream_t st) {
+                       int64_t* d2, double* out_est, Arena& ws, cudaStream_t st,
+                       jp_mlp* predictor) {
     const int64_t N = std::max<int64_t>(std::max(g.nr, g.ns), 1);
     *out_est = out_estimate((double)g.nx, g.out_join, (double)g.nr);
     if (mode == JP_FIXED) {
@@ -186,6 +187,13 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
         }
         *d1 = clamp_delta(a, N);
         *d2 = clamp_delta(b, N);
+        return;
+    }
+    if (mode == JP_LEARNED) {
+        if (!predictor) throw Error{JP_EINVAL, "JP_LEARNED needs a model (jp_set_predictor)"};
+        float f[128];
+        graph_features(g, f, ws, st);
+        mlp_predict(predictor, f, N, d1, d2);
         return;
     }
     if (mode != JP_COST_MODEL) throw Error{JP_EINVAL, "unknown threshold mode"};

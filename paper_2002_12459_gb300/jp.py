@@ -232,3 +232,127 @@ class Context:
         for name in arrays:
             d[name] = list(getattr(s, name))
         return d
+
+
+# ------------------------------------------------------------------ predictor
+JP_LEARNED = 3
+JP_MLP_PARAMS = 99330
+JP_MLP_MAX_BATCH = 1024
+_MODES["learned"] = JP_LEARNED
+
+
+def _bind_predictor(lib):
+    if getattr(lib, "_pred_bound", False):
+        return lib
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.jp_features.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel), fp]
+    lib.jp_features.restype = i32
+    lib.jp_set_predictor.argtypes = [vp, vp]
+    lib.jp_set_predictor.restype = i32
+    lib.jp_mlp_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    lib.jp_mlp_create.restype = i32
+    lib.jp_mlp_destroy.argtypes = [vp]
+    lib.jp_mlp_destroy.restype = None
+    lib.jp_mlp_set_params.argtypes = [vp, fp, i64]
+    lib.jp_mlp_set_params.restype = i32
+    lib.jp_mlp_get_params.argtypes = [vp, fp, i64]
+    lib.jp_mlp_get_params.restype = i32
+    lib.jp_mlp_forward.argtypes = [vp, fp, i32, fp]
+    lib.jp_mlp_forward.restype = i32
+    lib.jp_mlp_gradients.argtypes = [vp, fp, fp, i32, fp, fp]
+    lib.jp_mlp_gradients.restype = i32
+    lib.jp_mlp_train_step.argtypes = [vp, fp, fp, i32, ctypes.c_float, fp]
+    lib.jp_mlp_train_step.restype = i32
+    lib._pred_bound = True
+    return lib
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Predictor:
+    """The learned threshold predictor (jp_mlp_*): features -> (ln D1, ln D2)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import numpy as np
+        import torch
+        self._np = np
+        self.lib = _bind_predictor(load())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        rc = self.lib.jp_mlp_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != JP_OK:
+            raise JPError(rc, "jp_mlp_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.jp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != JP_OK:
+            raise JPError(rc, what)
+
+    def set_params(self, params):
+        p = self._np.ascontiguousarray(params, dtype=self._np.float32).ravel()
+        self._check(self.lib.jp_mlp_set_params(self.h, _fptr(p), p.size), "jp_mlp_set_params")
+
+    def get_params(self):
+        p = self._np.empty(JP_MLP_PARAMS, self._np.float32)
+        self._check(self.lib.jp_mlp_get_params(self.h, _fptr(p), p.size), "jp_mlp_get_params")
+        return p
+
+    def forward(self, X):
+        X = self._np.ascontiguousarray(X, dtype=self._np.float32)
+        Y = self._np.empty((X.shape[0], 2), self._np.float32)
+        self._check(self.lib.jp_mlp_forward(self.h, _fptr(X), X.shape[0], _fptr(Y)), "jp_mlp_forward")
+        return Y
+
+    def gradients(self, X, T):
+        X = self._np.ascontiguousarray(X, dtype=self._np.float32)
+        T = self._np.ascontiguousarray(T, dtype=self._np.float32)
+        g = self._np.empty(JP_MLP_PARAMS, self._np.float32)
+        loss = self._np.zeros(1, self._np.float32)
+        self._check(self.lib.jp_mlp_gradients(self.h, _fptr(X), _fptr(T), X.shape[0], _fptr(g),
+                                              _fptr(loss)), "jp_mlp_gradients")
+        return g, float(loss[0])
+
+    def train_step(self, X, T, lr):
+        X = self._np.ascontiguousarray(X, dtype=self._np.float32)
+        T = self._np.ascontiguousarray(T, dtype=self._np.float32)
+        loss = self._np.zeros(1, self._np.float32)
+        self._check(self.lib.jp_mlp_train_step(self.h, _fptr(X), _fptr(T), X.shape[0],
+                                               ctypes.c_float(lr), _fptr(loss)), "jp_mlp_train_step")
+        return float(loss[0])
+
+
+def _context_features(self, rx, ry, sz=None, sy=None):
+    """The 128 predictor features of the query on R (and S)."""
+    import numpy as np
+    _bind_predictor(self.lib)
+    R = _rel_of(rx, ry)
+    S = _rel_of(sz, sy) if sz is not None else None
+    out = np.empty(128, np.float32)
+    with self._torch.cuda.stream(self.stream):
+        rc = self.lib.jp_features(self.h, ctypes.byref(R), ctypes.byref(S) if S else None, _fptr(out))
+    self._check(rc)
+    return out
+
+
+def _context_set_predictor(self, pred):
+    _bind_predictor(self.lib)
+    self._predictor = pred
+    self._check(self.lib.jp_set_predictor(self.h, pred.h if pred is not None else None))
+
+
+Context.features = _context_features
+Context.set_predictor = _context_set_predictor

@@ -1,0 +1,167 @@
+"""Train the learned threshold predictor on thresholds the GPU method finds best.
+
+For each seeded power-law relation (N log-uniform, x and y degree exponents
+uniform in [1.2, 2.5], |dom x| = N/5, |dom y| = N/10) the two-path self-join
+is timed over a grid of fixed thresholds (device time of the whole query,
+best of two runs); the fastest grid point is the label (ln Delta1,
+ln Delta2) and the relation's 128 degree features (jp_features) the input.
+The network is trained with the library's own kernels (jp_mlp_train_step)
+and evaluated on held-out relations: the query time at the predicted
+thresholds is compared with the best grid time ("oracle-best threshold") and
+with the time at the cost-model thresholds (Algorithm 3), which is also the
+fallback when no model is set.
+
+  python -m paper_2002_12459_gb300.learn --train 160 --test 48 --out params.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+D1_GRID = (8, 16, 32, 64, 128, 256, 1024)
+D2_GRID = (4, 8, 16, 32, 64, 128, 512)
+
+
+def relation_spec(i: int, seed: int, n_lo: float, n_hi: float):
+    rng = np.random.default_rng(seed * 100003 + i)
+    n = int(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))))
+    gx, gy = rng.uniform(1.2, 2.5, 2)
+    return dict(n=n, dom_x=max(n // 5, 1), gamma_x=float(gx), dom_y=max(n // 10, 1),
+                gamma_y=float(gy), seed=seed * 100003 + i)
+
+
+def make_relation(spec):
+    from paper_2002_12459_gb300 import workloads as W
+    return W.powerlaw_relation(spec["n"], spec["dom_x"], spec["gamma_x"], spec["dom_y"],
+                               spec["gamma_y"], spec["seed"])
+
+
+def query_ms(ctx, dx, dy, mode, d1=1, d2=1, reps=2):
+    ctx.set_threshold(mode, d1, d2)
+    best = math.inf
+    st = None
+    for _ in range(reps):
+        ox, oz = ctx.two_path(dx, dy)
+        del ox, oz
+        st = ctx.stats()
+        best = min(best, st["ms_pass"][12])
+    return best, st
+
+
+def sweep(ctx, dx, dy):
+    times = {}
+    for d1 in D1_GRID:
+        for d2 in D2_GRID:
+            times[(d1, d2)] = query_ms(ctx, dx, dy, "fixed", d1, d2)[0]
+    return times
+
+
+def collect(ctx, specs, log):
+    import torch
+    feats, labels, rows = [], [], []
+    for k, spec in enumerate(specs):
+        x, y = make_relation(spec)
+        dx = torch.from_numpy(x).cuda()
+        dy = torch.from_numpy(y).cuda()
+        f = ctx.features(dx, dy)
+        times = sweep(ctx, dx, dy)
+        (b1, b2), tbest = min(times.items(), key=lambda kv: kv[1])
+        tcost, st = query_ms(ctx, dx, dy, "cost_model")
+        feats.append(f)
+        labels.append([math.log(b1), math.log(b2)])
+        rows.append(dict(spec=spec, best=(b1, b2), t_best=tbest, t_cost=tcost,
+                         cost_delta=(st["delta1"], st["delta2"]), x=dx, y=dy))
+        log(f"[learn] {k + 1}/{len(specs)} N={spec['n']} best={b1},{b2} {tbest:.2f} ms "
+            f"cost-model {tcost:.2f} ms")
+    return np.array(feats, np.float32), np.array(labels, np.float32), rows
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-initialised weights, zero biases, in the library's flat layout."""
+    rng = np.random.default_rng(seed)
+    dims = (128, 256, 256, 2)
+    parts = []
+    for i in range(3):
+        parts.append(rng.normal(0.0, math.sqrt(2.0 / dims[i]), (dims[i], dims[i + 1])).ravel())
+        parts.append(np.zeros(dims[i + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def fit(pred, X, T, steps: int, lr: float, seed: int, log):
+    pred.set_params(init_params(seed))
+    loss = None
+    for s in range(steps):
+        loss = pred.train_step(X, T, lr)
+        if s % 500 == 0 or s == steps - 1:
+            log(f"[learn] step {s}: loss {loss:.4f}")
+    return loss
+
+
+def evaluate(ctx, pred, rows, log):
+    ctx.set_predictor(pred)
+    out = []
+    for r in rows:
+        t_learn, st = query_ms(ctx, r["x"], r["y"], "learned")
+        out.append(dict(n=r["spec"]["n"], best=r["best"], t_best=r["t_best"], t_cost=r["t_cost"],
+                        t_learned=t_learn, learned_delta=(st["delta1"], st["delta2"]),
+                        cost_delta=r["cost_delta"]))
+    ctx.set_predictor(None)
+    ratio_l = [o["t_learned"] / o["t_best"] for o in out]
+    ratio_c = [o["t_cost"] / o["t_best"] for o in out]
+    summary = dict(relations=len(out),
+                   learned_over_best_geomean=float(np.exp(np.mean(np.log(ratio_l)))),
+                   cost_over_best_geomean=float(np.exp(np.mean(np.log(ratio_c)))),
+                   learned_total_ms=float(sum(o["t_learned"] for o in out)),
+                   cost_total_ms=float(sum(o["t_cost"] for o in out)),
+                   best_total_ms=float(sum(o["t_best"] for o in out)))
+    log(f"[learn] held-out: learned/best {summary['learned_over_best_geomean']:.3f}, "
+        f"cost-model/best {summary['cost_over_best_geomean']:.3f}")
+    return summary, out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=160)
+    ap.add_argument("--test", type=int, default=48)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--n-lo", type=float, default=1e5)
+    ap.add_argument("--n-hi", type=float, default=1e6)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default=None, help="write the trained float32 parameters (.npy)")
+    ap.add_argument("--report", default=None, help="write a JSON report")
+    args = ap.parse_args(argv)
+
+    from paper_2002_12459_gb300 import build, jp
+    build.build()
+
+    def log(*a):
+        print(*a, file=sys.stderr, flush=True)
+
+    ctx = jp.Context(0)
+    pred = jp.Predictor(0)
+    t0 = time.time()
+    specs = [relation_spec(i, args.seed, args.n_lo, args.n_hi) for i in range(args.train + args.test)]
+    X, T, rows = collect(ctx, specs, log)
+    Xtr, Ttr = X[:args.train], T[:args.train]
+    loss = fit(pred, Xtr, Ttr, args.steps, args.lr, args.seed, log)
+    summary, detail = evaluate(ctx, pred, rows[args.train:], log)
+    summary.update(train_relations=args.train, final_train_loss=loss,
+                   seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
+    if args.out:
+        np.save(args.out, pred.get_params())
+    if args.report:
+        with open(args.report, "w") as f:
+            json.dump(dict(summary=summary, held_out=detail), f, indent=1, default=str)
+    print(json.dumps(summary))
+    pred.close()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
