@@ -62,6 +62,8 @@ void* Arena::carve(size_t bytes) {
     for (auto& c : chunks) total += c.size;
     size_t sz = bytes;
     if (sz < total) sz = total;
+    if (sz < hint) sz = hint;
+    hint = 0;
     if (sz < ((size_t)64 << 20)) sz = (size_t)64 << 20;
     void* p = raw_alloc(sz);
     if (!p) throw Error{JP_ENOMEM, "workspace allocation of " + std::to_string(sz) + " bytes failed"};
@@ -71,6 +73,18 @@ void* Arena::carve(size_t bytes) {
     used += bytes;
     if (used > peak) peak = used;
     return p;
+}
+
+void Arena::begin() {
+    size_t held = 0;
+    for (auto& c : chunks) held += c.size;
+    const size_t need = peak;
+    if (chunks.size() > 1 || (held > ((size_t)1 << 30) && 2 * need < held)) {
+        release_all();
+        hint = need;
+    }
+    reset();
+    peak = 0;
 }
 
 void Arena::release_all() {
@@ -227,7 +241,7 @@ int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
     try {
         JP_CUDA_TRY(cudaSetDevice(ctx->device));
         cudaStream_t st = ctx->stream;
-        ctx->ws.reset();
+        ctx->ws.begin();
         const int64_t launches0 = jp::g_launches;
         JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
         for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
@@ -352,7 +366,7 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
     try {
         JP_CUDA_TRY(cudaSetDevice(ctx->device));
         cudaStream_t st = ctx->stream;
-        ctx->ws.reset();
+        ctx->ws.begin();
         const int64_t launches0 = jp::g_launches;
         JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
         for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
@@ -454,7 +468,7 @@ int jp_features(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, float* out128) {
     try {
         JP_CUDA_TRY(cudaSetDevice(ctx->device));
         cudaStream_t st = ctx->stream;
-        ctx->ws.reset();
+        ctx->ws.begin();
         JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
         jp_rel Rd = to_device(ctx, R);
         jp_rel Sd;

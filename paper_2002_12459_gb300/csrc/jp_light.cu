@@ -32,7 +32,7 @@ namespace {
 
 constexpr int32_t KEY_PAD = 0x7fffffff;
 constexpr int W_CAP = 256;            // small warp class capacity
-constexpr int W2_CAP = 2048;          // large warp class capacity
+constexpr int W2_CAP = 2048;          // warp bucket class capacity
 constexpr int BM_THREADS = 1024;
 constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
 constexpr int BM_WARP_PER_LIST = 128;    // rows with this many neighbours: warp per list
@@ -97,7 +97,7 @@ __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
     const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 2 + 2 * NQ; i += blockDim.x) s_sum[i] = 0;
     __syncthreads();
-    unsigned long long need = 0, cands = 0, qc[NQ] = {0, 0, 0, 0}, qd[NQ] = {0, 0, 0, 0};
+    unsigned long long need = 0, cands = 0, qc[NQ] = {}, qd[NQ] = {};
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nx;
          base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = base + threadIdx.x;
@@ -467,11 +467,11 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
         unsigned long long ub = (unsigned long long)A.cand[a] +
                                 (heavy ? (unsigned long long)A.w : 0ull);
         if (ub > (unsigned long long)A.nz) ub = (unsigned long long)A.nz;
+        // the reservation's result is read only after the marking phase's
+        // barrier, so its latency overlaps the marking
         if (threadIdx.x == 0) s_base = atomicAdd(&A.ctr->cursor, ub);
-        __syncthreads();
-        const unsigned long long base = s_base;
-        const bool room = base + ub <= (unsigned long long)A.tmp_cap;
-        if (!room && threadIdx.x == 0) atomicOr(A.status, ST_OVERFLOW);
+        unsigned long long base = 0;
+        bool room = true;
         unsigned long long running = 0;
         for (int64_t z0 = 0; z0 < A.nz; z0 += win_bits) {
             const int64_t zend = min(A.nz, z0 + win_bits);
@@ -569,6 +569,9 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 }
             }
             __syncthreads();
+            base = s_base;
+            room = base + ub <= (unsigned long long)A.tmp_cap;
+            if (!room && z0 == 0 && threadIdx.x == 0) atomicOr(A.status, ST_OVERFLOW);
             // emit set bits in z order: blocked ranges of summary words
             const int32_t spt = (nsumm + blockDim.x - 1) / blockDim.x;
             const int32_t lo = min(nsumm, (int32_t)threadIdx.x * spt);
