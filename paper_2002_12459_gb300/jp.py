@@ -302,6 +302,15 @@ class Predictor:
         if rc != JP_OK:
             raise JPError(rc, what)
 
+    @classmethod
+    def trained(cls, device: int = 0, stream=None):
+        """A predictor holding the shipped parameters (predictor/params.npy,
+        written by ``python -m paper_2002_12459_gb300.learn --out``)."""
+        import numpy as np
+        p = cls(device, stream)
+        p.set_params(np.load(os.path.join(PKG, "predictor", "params.npy")))
+        return p
+
     def set_params(self, params):
         p = self._np.ascontiguousarray(params, dtype=self._np.float32).ravel()
         self._check(self.lib.jp_mlp_set_params(self.h, _fptr(p), p.size), "jp_mlp_set_params")

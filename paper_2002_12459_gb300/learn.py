@@ -53,29 +53,99 @@ def query_ms(ctx, dx, dy, mode, d1=1, d2=1, reps=2):
     return best, st
 
 
-def sweep(ctx, dx, dy):
+def heavy_bound(x, y, d1, d2):
+    """Upper bounds (u, v) of the heavy block at (d1, d2): x of degree > d2, y
+    of degree > d1 (self-join, so w = u)."""
+    _, cx = np.unique(x, return_counts=True)
+    _, cy = np.unique(y, return_counts=True)
+    return int((cx > d2).sum()), int((cy > d1).sum())
+
+
+# grid points whose heavy block is beyond these bounds are not run (their time
+# is taken as infinite): operands over 16 GB, or a product over ~2 s
+MAX_BLOCK_BYTES = 16e9
+MAX_BLOCK_OPS = 4e15
+
+
+def sweep(ctx, dx, dy, x, y, log=None):
+    import torch
+    from paper_2002_12459_gb300 import jp
     times = {}
     for d1 in D1_GRID:
         for d2 in D2_GRID:
-            times[(d1, d2)] = query_ms(ctx, dx, dy, "fixed", d1, d2)[0]
+            u, v = heavy_bound(x, y, d1, d2)
+            if 2.0 * u * v > MAX_BLOCK_BYTES or 2.0 * u * v * u > MAX_BLOCK_OPS:
+                times[(d1, d2)] = math.inf
+                continue
+            try:
+                times[(d1, d2)] = query_ms(ctx, dx, dy, "fixed", d1, d2)[0]
+            except jp.JPError as e:      # out of device memory at this grid point
+                times[(d1, d2)] = math.inf
+                torch.cuda.empty_cache()
+                if log:
+                    log(f"[learn] grid point {d1},{d2}: {e}")
     return times
+
+
+def join_size(x, y) -> float:
+    """sum_y deg(y)^2 of the distinct tuples (the self-join's full join size)."""
+    key = np.unique(x.astype(np.int64) * (1 << 32) + (y.astype(np.int64) & 0xFFFFFFFF))
+    d = np.unique(key & 0xFFFFFFFF, return_counts=True)[1].astype(np.float64)
+    return float((d * d).sum())
+
+
+def _draw_one(args):
+    """(spec, x, y) of relation i, or (spec, None, reason) when it is rejected."""
+    i, seed, n_lo, n_hi, max_join = args
+    spec = relation_spec(i, seed, n_lo, n_hi)
+    try:
+        x, y = make_relation(spec)
+    except RuntimeError as e:   # the degree targets admit too few distinct tuples
+        return spec, None, str(e)
+    oj = join_size(x, y)
+    if oj > max_join:
+        return spec, None, f"full join {oj:.3g} > {max_join:.3g}"
+    spec["out_join"] = oj
+    return spec, x, y
+
+
+def draw_specs(count, seed, n_lo, n_hi, max_join, log, workers=None):
+    """The first `count` seeded relations (spec, x, y) whose full join is at
+    most max_join (heavier tails give outputs beyond one GPU's memory).
+    Relations are drawn by a pool of spawned processes, in index order; call
+    this before the first GPU call of the process."""
+    import multiprocessing as mp
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    out, i = [], 0
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+        while len(out) < count:
+            batch = [(j, seed, n_lo, n_hi, max_join) for j in range(i, i + 2 * workers)]
+            for (j, *_), (spec, x, y) in zip(batch, pool.map(_draw_one, batch)):
+                if x is None:
+                    log(f"[learn] skip relation {j}: {y}")
+                elif len(out) < count:
+                    out.append((spec, x, y))
+            i += len(batch)
+    return out
 
 
 def collect(ctx, specs, log):
     import torch
     feats, labels, rows = [], [], []
-    for k, spec in enumerate(specs):
-        x, y = make_relation(spec)
+    for k, (spec, x, y) in enumerate(specs):
         dx = torch.from_numpy(x).cuda()
         dy = torch.from_numpy(y).cuda()
         f = ctx.features(dx, dy)
-        times = sweep(ctx, dx, dy)
+        times = sweep(ctx, dx, dy, x, y, log)
         (b1, b2), tbest = min(times.items(), key=lambda kv: kv[1])
         tcost, st = query_ms(ctx, dx, dy, "cost_model")
         feats.append(f)
         labels.append([math.log(b1), math.log(b2)])
         rows.append(dict(spec=spec, best=(b1, b2), t_best=tbest, t_cost=tcost,
                          cost_delta=(st["delta1"], st["delta2"]), x=dx, y=dy))
+        torch.cuda.empty_cache()
         log(f"[learn] {k + 1}/{len(specs)} N={spec['n']} best={b1},{b2} {tbest:.2f} ms "
             f"cost-model {tcost:.2f} ms")
     return np.array(feats, np.float32), np.array(labels, np.float32), rows
@@ -130,8 +200,9 @@ def main(argv=None):
     ap.add_argument("--test", type=int, default=48)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--n-lo", type=float, default=1e5)
-    ap.add_argument("--n-hi", type=float, default=1e6)
+    ap.add_argument("--n-hi", type=float, default=5e5)
     ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--max-join", type=float, default=1e9)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None, help="write the trained float32 parameters (.npy)")
     ap.add_argument("--report", default=None, help="write a JSON report")
@@ -143,10 +214,11 @@ def main(argv=None):
     def log(*a):
         print(*a, file=sys.stderr, flush=True)
 
+    t0 = time.time()
+    # the relations are drawn by spawned workers before this process touches the GPU
+    specs = draw_specs(args.train + args.test, args.seed, args.n_lo, args.n_hi, args.max_join, log)
     ctx = jp.Context(0)
     pred = jp.Predictor(0)
-    t0 = time.time()
-    specs = [relation_spec(i, args.seed, args.n_lo, args.n_hi) for i in range(args.train + args.test)]
     X, T, rows = collect(ctx, specs, log)
     Xtr, Ttr = X[:args.train], T[:args.train]
     loss = fit(pred, Xtr, Ttr, args.steps, args.lr, args.seed, log)
