@@ -149,7 +149,10 @@ def cpu_baseline(rx, ry, target_cand=3.0e7):
 
 # ----------------------------------------------------------------- roofline
 KERNEL_SLOTS = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>",
-                7: "light_bucket_kernel<2048,256>", 9: "light_bitmap_kernel", 11: "place_kernel"}
+                7: "light_bucket_kernel<2048,256>", 8: "light_merge_kernel",
+                9: "light_bitmap_kernel", 11: "place_kernel"}
+# timer slot -> light class index of jp_stats.light_* arrays
+SLOT_CLASS = {6: (0,), 7: (1,), 8: (4, 5), 9: (3,)}
 
 
 def kernel_roofline(slot, st, peaks, peak_kind, ms):
@@ -169,11 +172,11 @@ def kernel_roofline(slot, st, peaks, peak_kind, ms):
         k = st.get("k", 2)
         byts = (8.0 + 4.0 * k) * out + 20.0 * st["dom_x"]
     else:
-        q = slot - 6
         # candidates gathered (4 B), neighbour lists and per-x records read
         # (4 B each), distinct values written (bounded by the candidates)
-        byts = 4.0 * st["light_cand"][q] + 4.0 * (st["light_x"][q] + st["light_deg"][q])
-        byts += 4.0 * min(st["light_cand"][q], out)
+        cand = sum(st["light_cand"][q] for q in SLOT_CLASS[slot])
+        nxq = sum(st["light_x"][q] + st["light_deg"][q] for q in SLOT_CLASS[slot])
+        byts = 4.0 * cand + 4.0 * nxq + 4.0 * min(cand, out)
     ach = byts / (ms * 1e-3) / 1e9
     return {"kernel": KERNEL_SLOTS[slot], "ms": ms, "bound": "hbm", "achieved": ach, "peak": hbm,
             "unit": "GB/s", "frac": ach / hbm, "traffic": None,

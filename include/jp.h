@@ -93,15 +93,18 @@ typedef struct {
     int64_t out_count;         /* |OUT| */
     int64_t heavy_pairs;       /* nonzeros of the heavy product (0 if not counted) */
     int64_t kernel_launches;   /* kernels the library launched for the query */
-    int64_t light_x[4];        /* x values per light class: warp <= 256, warp <= 2048, unused, bitmap */
-    int64_t light_cand[4];     /* candidates enumerated per light class */
-    int64_t light_deg[4];      /* neighbour-list entries read per light class */
+    int64_t light_x[8];        /* x values per light class: 0 warp sort (c <= 256), 1 bucket sort
+                                  (c <= 2048), 2 single list copied in place, 3 bitmap (larger c,
+                                  and every heavy x), 4 and 5 merge of sorted lists (c <= 4096,
+                                  c <= 8192), 6-7 unused */
+    int64_t light_cand[8];     /* candidates enumerated per light class */
+    int64_t light_deg[8];      /* neighbour-list entries read per light class */
     double  ms_total;          /* host wall time of the call */
     double  ms_pass[16];       /* device ms (CUDA events on the query stream) of:
                                   0 index build, 1 threshold selection, 2 partition,
                                   3 matrix build, 4 heavy GEMM kernel, 5 light
-                                  classification, 6-9 light kernels (warp <= 256,
-                                  warp <= 2048, unused, bitmap+union), 10 output count,
+                                  classification, 6-9 light kernels (warp sort,
+                                  bucket sort, merge, bitmap+union), 10 output count,
                                   11 output placement kernel, 12 whole query */
 } jp_stats;
 

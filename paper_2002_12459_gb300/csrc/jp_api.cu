@@ -321,7 +321,7 @@ int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
         s.light_candidates = lr.candidates;
         s.out_count = count;
         s.kernel_launches = jp::g_launches - launches0;
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             s.light_x[q] = lr.class_x[q];
             s.light_cand[q] = lr.class_cand[q];
             s.light_deg[q] = lr.class_deg[q];
@@ -430,7 +430,7 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         s.light_candidates = lr.candidates;
         s.out_count = count;
         s.kernel_launches = jp::g_launches - launches0;
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             s.light_x[q] = lr.class_x[q];
             s.light_cand[q] = lr.class_cand[q];
             s.light_deg[q] = lr.class_deg[q];

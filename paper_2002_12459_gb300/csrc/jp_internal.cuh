@@ -167,9 +167,10 @@ struct LightResult {
     int32_t* tmp = nullptr;
     int64_t tmp_cap = 0;
     int64_t candidates = 0;
-    int64_t class_x[4] = {0, 0, 0, 0};     // x per class: warp, 2K block, 16K block, bitmap
-    int64_t class_cand[4] = {0, 0, 0, 0};  // candidates per class
-    int64_t class_deg[4] = {0, 0, 0, 0};   // neighbour entries per class
+    // per class: warp sort, bucket sort, single-list copy, bitmap, merge 4096, merge 8192
+    int64_t class_x[8] = {};      // x values
+    int64_t class_cand[8] = {};   // candidates
+    int64_t class_deg[8] = {};    // neighbour entries
     int32_t* tile_x = nullptr;             // x holding the first output of each output tile
 };
 void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightResult& lr,
@@ -210,7 +211,7 @@ int grid_for(int64_t n, int block, int max_blocks = 152 * 32);
 // begin/end pair per pass or kernel (reported in jp_stats.ms_pass).
 enum TimerSlot {
     TM_BUILD = 0, TM_SELECT, TM_PARTITION, TM_PACK, TM_GEMM, TM_CLASSIFY, TM_LIGHT_WARP,
-    TM_LIGHT_C2, TM_LIGHT_C16, TM_LIGHT_BITMAP, TM_COUNT, TM_PLACE, TM_TOTAL, TM_SLOTS = 16
+    TM_LIGHT_C2, TM_LIGHT_MERGE, TM_LIGHT_BITMAP, TM_COUNT, TM_PLACE, TM_TOTAL, TM_SLOTS = 16
 };
 struct Timer {
     cudaEvent_t b[TM_SLOTS] = {}, e[TM_SLOTS] = {};

@@ -16,6 +16,9 @@
 //                 and distinct: the output pass copies S[b] in place
 //   c <= 256      a warp sorts the candidates in shared memory (bitonic)
 //   c <= 2048     a warp bucket-sorts them over the z domain (linear work)
+//   c <= 8192     (at most 64 lists) a block merges the lists, which are
+//                 already sorted, pairwise in shared memory (two buffer sizes,
+//                 4096 and 8192)
 //   larger, and every heavy x: a block marks z in a shared-memory bitmap
 //                 over the z domain (windowed when the domain is larger than
 //                 shared memory) with a one-bit-per-word summary, so that
@@ -33,11 +36,15 @@ namespace {
 constexpr int32_t KEY_PAD = 0x7fffffff;
 constexpr int W_CAP = 256;            // small warp class capacity
 constexpr int W2_CAP = 2048;          // warp bucket class capacity
+constexpr int M_CAP = 4096;           // merge class capacity (one block per x)
+constexpr int M2_CAP = 8192;          // larger merge class capacity
+constexpr int M_THREADS = 256;
+constexpr int M_MAXL = 64;            // merge class: at most this many neighbour lists
 constexpr int BM_THREADS = 1024;
 constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
 constexpr int BM_WARP_PER_LIST = 128;    // rows with this many neighbours: warp per list
 
-enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, NQ = 4 };
+enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, Q_MERGE = 4, Q_MERGE2 = 5, NQ = 6 };
 
 struct Counters {
     unsigned long long cursor;        // scratch cursor
@@ -105,8 +112,13 @@ __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
         unsigned long long c = 0, ub = 0;
         if (a < nx) {
             const bool heavy = hx[a] >= 0;
+            const int32_t dg = rxoff[a + 1] - rxoff[a];
             c = (unsigned long long)cand[a];
-            if (heavy || (c > (unsigned long long)W2_CAP && rxoff[a + 1] - rxoff[a] > 1)) {
+            if (!heavy && c > (unsigned long long)W2_CAP && c <= (unsigned long long)M2_CAP &&
+                dg > 1 && dg <= M_MAXL) {
+                q = c <= (unsigned long long)M_CAP ? Q_MERGE : Q_MERGE2;
+                ub = c;
+            } else if (heavy || (c > (unsigned long long)W2_CAP && dg > 1)) {
                 q = Q_BITMAP;
                 ub = c + (heavy ? (unsigned long long)w : 0ull);
                 if (ub > (unsigned long long)nz) ub = (unsigned long long)nz;
@@ -437,6 +449,183 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
     }
 }
 
+// ------------------------------------------------------------ merge class
+// One block per light x with W2_CAP < c <= M_CAP and 2..M_MAXL neighbour
+// lists.  Every S[b] is already sorted, so the candidates are deg sorted runs:
+// they are gathered into shared memory run after run, merged pairwise
+// (ceil(log2 deg) levels; in each level every thread produces a fixed share of
+// the outputs, starting at the co-rank found by a merge-path search), and the
+// merged sequence is deduplicated by comparing neighbours.  Work is linear in
+// c per level and the output is written with coalesced stores.
+// number of elements of A among the first d outputs of merge(A, B), where
+// ties take A first
+__device__ __forceinline__ int32_t co_rank(const int32_t* A, int32_t la, const int32_t* B,
+                                           int32_t lb, int32_t d) {
+    int32_t lo = max(0, d - lb), hi = min(d, la);
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (A[mid] <= B[d - mid - 1]) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(M_THREADS)
+    light_merge_kernel(LightArgs A, const int32_t* queue, const Counters* qc, int qid) {
+    extern __shared__ int32_t dyn_m[];
+    __shared__ int32_t s_runs[2][M_MAXL + 1];   // run boundaries, current and next level
+    __shared__ int32_t s_start[M_MAXL];         // list starts in szcol
+    __shared__ uint32_t s_wsum[M_THREADS / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nq = qc->q[qid];
+    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
+        const int32_t a = queue[qi];
+        const int32_t e0 = A.rxoff[a], deg = A.rxoff[a + 1] - e0;
+        if (deg < 1 || deg > M_MAXL) {   // cannot happen: the class bounds the degree
+            if (tid == 0) atomicOr(A.status, ST_BADINDEX);
+            continue;
+        }
+        // run boundaries: warp 0, two lists per lane
+        if (warp == 0) {
+            int32_t L0 = 0, L1 = 0, st0 = 0, st1 = 0;
+            const int i0 = 2 * lane, i1 = 2 * lane + 1;
+            if (i0 < deg) {
+                const int32_t b = A.rycol[e0 + i0];
+                st0 = A.syoff[b];
+                L0 = A.syoff[b + 1] - st0;
+            }
+            if (i1 < deg) {
+                const int32_t b = A.rycol[e0 + i1];
+                st1 = A.syoff[b];
+                L1 = A.syoff[b + 1] - st1;
+            }
+            int32_t inc = L0 + L1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int32_t ex = inc - L0 - L1;
+            if (lane == 0) s_runs[0][0] = 0;
+            if (i0 < deg) { s_runs[0][i0 + 1] = ex + L0; s_start[i0] = st0; }
+            if (i1 < deg) { s_runs[0][i1 + 1] = ex + L0 + L1; s_start[i1] = st1; }
+        }
+        __syncthreads();
+        const int32_t c = s_runs[0][deg];
+        if (c > CAP) {                   // cannot happen: the class bounds c
+            if (tid == 0) atomicOr(A.status, ST_BADINDEX);
+            __syncthreads();
+            continue;
+        }
+        // the reservation (c slots, an upper bound of the distinct count) is
+        // read only after the merge, so its latency overlaps it
+        if (tid == 0) s_base = atomicAdd(&A.ctr->cursor, (unsigned long long)c);
+        int32_t* src = dyn_m;
+        int32_t* dst = dyn_m + CAP;
+        // gather: flat candidate f of run k is S[b_k][f - run_k]
+        constexpr int U = 8;
+        for (int32_t f0 = tid; f0 < c; f0 += U * M_THREADS) {
+            int32_t zz[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t f = f0 + u * M_THREADS;
+                zz[u] = 0;
+                if (f < c) {
+                    int32_t lo = 0, hi = deg;    // last k with s_runs[0][k] <= f
+                    while (hi - lo > 1) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (s_runs[0][mid] <= f) lo = mid; else hi = mid;
+                    }
+                    zz[u] = A.szcol[s_start[lo] + (f - s_runs[0][lo])];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t f = f0 + u * M_THREADS;
+                if (f < c) src[f] = zz[u];
+            }
+        }
+        __syncthreads();
+        // pairwise merge levels
+        int runs = deg, cur = 0;
+        const int32_t per = (c + M_THREADS - 1) / M_THREADS;
+        while (runs > 1) {
+            const int32_t* rb = s_runs[cur];
+            const int pairs = (runs + 1) >> 1;
+            if (tid <= pairs) s_runs[cur ^ 1][tid] = tid < pairs ? rb[2 * tid] : c;
+            int32_t o = min(c, tid * per);
+            const int32_t o_end = min(c, o + per);
+            while (o < o_end) {
+                int lo = 0, hi = pairs;          // pair p with rb[2p] <= o < its end
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (rb[2 * mid] <= o) lo = mid; else hi = mid;
+                }
+                const int32_t a0 = rb[2 * lo], a1 = rb[min(2 * lo + 1, runs)],
+                              b1 = rb[min(2 * lo + 2, runs)];
+                const int32_t seg_end = min(o_end, b1);
+                const int32_t i = co_rank(src + a0, a1 - a0, src + a1, b1 - a1, o - a0);
+                int32_t ia = a0 + i, ib = a1 + (o - a0 - i);
+                int32_t va = ia < a1 ? src[ia] : INT32_MAX;
+                int32_t vb = ib < b1 ? src[ib] : INT32_MAX;
+                for (; o < seg_end; ++o) {       // z ids are below INT32_MAX
+                    // branch-free step: one shared-memory load per output
+                    const bool ta = va <= vb;
+                    dst[o] = ta ? va : vb;
+                    ia += ta;
+                    ib += !ta;
+                    const int32_t ni = ta ? ia : ib;
+                    const int32_t nv = ni < (ta ? a1 : b1) ? src[ni] : INT32_MAX;
+                    va = ta ? nv : va;
+                    vb = ta ? vb : nv;
+                }
+            }
+            __syncthreads();
+            int32_t* t = src;
+            src = dst;
+            dst = t;
+            cur ^= 1;
+            runs = pairs;
+        }
+        // deduplicate neighbours: warp w owns a range of whole 32-value rounds
+        const int32_t rounds = (c + 31) >> 5;
+        const int32_t rpw = (rounds + (M_THREADS / 32) - 1) / (M_THREADS / 32);
+        const int32_t wb = min(c, warp * rpw * 32), we = min(c, wb + rpw * 32);
+        uint32_t mine = 0;
+        for (int32_t i = wb + lane; i - lane < we; i += 32) {
+            const bool keep = i < we && (i == 0 || src[i] != src[i - 1]);
+            mine += __popc(__ballot_sync(0xffffffffu, keep));
+        }
+        if (lane == 0) s_wsum[warp] = mine;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < M_THREADS / 32; ++k) {
+            const uint32_t v = s_wsum[k];
+            before += k < warp ? v : 0u;
+            total += v;
+        }
+        const unsigned long long base = s_base;
+        const bool room = base + (unsigned long long)c <= (unsigned long long)A.tmp_cap;
+        if (room) {
+            uint32_t pos = before;
+            for (int32_t i = wb + lane; i - lane < we; i += 32) {
+                const bool keep = i < we && (i == 0 || src[i] != src[i - 1]);
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) A.tmp[base + pos + __popc(m & ((1u << lane) - 1u))] = src[i];
+                pos += __popc(m);
+            }
+        }
+        if (tid == 0) {
+            if (!room) atomicOr(A.status, ST_OVERFLOW);
+            A.cnt[a] = room ? (int32_t)total : 0;
+            A.tmp_off[a] = (int64_t)base;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ bitmap class
 __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, int32_t r) {
     const int32_t wi = r >> 5;
@@ -692,6 +881,32 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
             A, queues + (int64_t)Q_W2 * nx, ctr, Q_W2);
         JP_CHECK_LAUNCH();
         tend(TM_LIGHT_C2);
+    }
+    if (hc.q[Q_MERGE] || hc.q[Q_MERGE2]) {
+        // 2 CAP ints of shared memory per block: 32 KB (6 blocks per SM) and
+        // 64 KB (3 blocks per SM)
+        const size_t sm1 = (size_t)2 * M_CAP * sizeof(int32_t);
+        const size_t sm2 = (size_t)2 * M2_CAP * sizeof(int32_t);
+        static bool attrm = false;
+        if (!attrm) {
+            JP_CUDA_TRY(cudaFuncSetAttribute(light_merge_kernel<M_CAP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+            JP_CUDA_TRY(cudaFuncSetAttribute(light_merge_kernel<M2_CAP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+            attrm = true;
+        }
+        tbegin(TM_LIGHT_MERGE);
+        if (hc.q[Q_MERGE2]) {
+            light_merge_kernel<M2_CAP><<<grid_for(hc.q[Q_MERGE2], 1, 152 * 3), M_THREADS, sm2, st>>>(
+                A, queues + (int64_t)Q_MERGE2 * nx, ctr, Q_MERGE2);
+            JP_CHECK_LAUNCH();
+        }
+        if (hc.q[Q_MERGE]) {
+            light_merge_kernel<M_CAP><<<grid_for(hc.q[Q_MERGE], 1, 152 * 6), M_THREADS, sm1, st>>>(
+                A, queues + (int64_t)Q_MERGE * nx, ctr, Q_MERGE);
+            JP_CHECK_LAUNCH();
+        }
+        tend(TM_LIGHT_MERGE);
     }
     if (hc.q[Q_BITMAP]) {
         int64_t words = (g.nz + 31) / 32;

@@ -86,25 +86,40 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
         if (threadIdx.x == 0) s_off[nxs] = (xhi < nx) ? out_off[xhi] : count;
     }
     __syncthreads();
-#pragma unroll 2
+    // all of a thread's list reads, then all of its id -> value gathers, then
+    // the stores: OUT_VT independent loads in flight per phase
+    int32_t zid[OUT_VT], xv[OUT_VT], xv2[OUT_VT];
+#pragma unroll
     for (int k = 0; k < OUT_VT; ++k) {
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
-        if (o > o_last) break;
-        int32_t z, xv, xv2 = 0;
-        if (staged) {
-            const int64_t i = find_x(s_off, 0, nxs, o);
-            z = list_at(tmp, szcol, s_toff[i], o - s_off[i]);
-            xv = s_xv[i];
-            if (xval2) xv2 = s_xv2[i];
-        } else {
-            const int64_t x = find_x(out_off, xlo, xhi, o);
-            z = list_at(tmp, szcol, tmp_off[x], o - out_off[x]);
-            xv = xval[x];
-            if (xval2) xv2 = xval2[x];
+        zid[k] = -1;
+        xv[k] = 0;
+        xv2[k] = 0;
+        if (o <= o_last) {
+            if (staged) {
+                const int64_t i = find_x(s_off, 0, nxs, o);
+                zid[k] = list_at(tmp, szcol, s_toff[i], o - s_off[i]);
+                xv[k] = s_xv[i];
+                if (xval2) xv2[k] = s_xv2[i];
+            } else {
+                const int64_t x = find_x(out_off, xlo, xhi, o);
+                zid[k] = list_at(tmp, szcol, tmp_off[x], o - out_off[x]);
+                xv[k] = xval[x];
+                if (xval2) xv2[k] = xval2[x];
+            }
         }
-        out_x[o] = xv;
-        if (out_x2) out_x2[o] = xv2;
-        out_z[o] = zval[z];
+    }
+    int32_t zv[OUT_VT];
+#pragma unroll
+    for (int k = 0; k < OUT_VT; ++k) zv[k] = zid[k] >= 0 ? zval[zid[k]] : 0;
+#pragma unroll
+    for (int k = 0; k < OUT_VT; ++k) {
+        const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
+        if (o <= o_last) {
+            out_x[o] = xv[k];
+            if (out_x2) out_x2[o] = xv2[k];
+            out_z[o] = zv[k];
+        }
     }
 }
 

@@ -52,8 +52,8 @@ class jp_stats(ctypes.Structure):
                 ("v", ctypes.c_int64), ("w", ctypes.c_int64),
                 ("light_candidates", ctypes.c_int64), ("out_count", ctypes.c_int64),
                 ("heavy_pairs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("light_x", ctypes.c_int64 * 4), ("light_cand", ctypes.c_int64 * 4),
-                ("light_deg", ctypes.c_int64 * 4),
+                ("light_x", ctypes.c_int64 * 8), ("light_cand", ctypes.c_int64 * 8),
+                ("light_deg", ctypes.c_int64 * 8),
                 ("ms_total", ctypes.c_double),
                 ("ms_pass", ctypes.c_double * 16)]
 

@@ -160,3 +160,38 @@ def test_bitmap_window_wider_than_shared_memory(ctx, oracle_mod):
     # each base x shares its y with two others (3 pairs); the 18 base x on the
     # six special y gain the special x; each special x reaches 3 * 3 + 1 z
     assert len(ox) == 3 * n + 18 + 2 * 10
+
+
+def _class_relation(seed):
+    """x rows whose candidate counts span every light class: y values of
+    degree 40..400, x rows of 1..70 neighbour lists (c from a few to ~20k)."""
+    rng = np.random.default_rng(seed)
+    ny = 400
+    ydeg = rng.integers(40, 400, ny)
+    xs, ys = [], []
+    nx = 3000
+    for a in range(nx):
+        d = int(rng.choice([1, 2, 3, 6, 12, 20, 40, 64, 70]))
+        ys.append(rng.choice(ny, min(d, ny), replace=False, p=ydeg / ydeg.sum()))
+        xs.append(np.full(len(ys[-1]), a))
+    rx = np.concatenate(xs).astype(np.int32)
+    ry = np.concatenate(ys).astype(np.int32)
+    # top up every y to its degree with extra x values (they are light rows too)
+    have = np.bincount(ry, minlength=ny)
+    extra_y = np.repeat(np.arange(ny), np.maximum(ydeg - have, 0))
+    extra_x = nx + np.arange(len(extra_y))
+    return (np.concatenate([rx, extra_x.astype(np.int32)]),
+            np.concatenate([ry, extra_y.astype(np.int32)]))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_every_light_class(ctx, oracle_mod, seed):
+    rx, ry = _class_relation(seed)
+    want = oracle_mod.two_path(rx, ry)
+    # all light: the warp, bucket, copy, bitmap and both merge classes are used
+    assert_same(run(ctx, rx, ry, d1=10 ** 6, d2=10 ** 6), want)
+    st = ctx.stats()
+    assert all(st["light_x"][q] > 0 for q in range(6)), st["light_x"]
+    # heavy x and heavy y mixed in
+    for d1, d2 in [(200, 30), (60, 8), (350, 65)]:
+        assert_same(run(ctx, rx, ry, d1=d1, d2=d2), want)
