@@ -96,7 +96,8 @@ typedef struct {
     int64_t light_x[8];        /* x values per light class: 0 warp sort (c <= 256), 1 bucket sort
                                   (c <= 2048), 2 single list copied in place, 3 bitmap (larger c,
                                   and every heavy x), 4 and 5 merge of sorted lists (c <= 4096,
-                                  c <= 8192), 6-7 unused */
+                                  c <= 8192), 6 bitmap hubs (>= 128 lists or >= 65536
+                                  candidates), 7 unused */
     int64_t light_cand[8];     /* candidates enumerated per light class */
     int64_t light_deg[8];      /* neighbour-list entries read per light class */
     double  ms_total;          /* host wall time of the call */

@@ -44,7 +44,8 @@ constexpr int BM_THREADS = 1024;
 constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
 constexpr int BM_WARP_PER_LIST = 128;    // rows with this many neighbours: warp per list
 
-enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, Q_MERGE = 4, Q_MERGE2 = 5, NQ = 6 };
+enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, Q_MERGE = 4, Q_MERGE2 = 5, Q_HUB = 6, NQ = 7 };
+constexpr int64_t HUB_CAND = 65536;      // bitmap rows with this many candidates are hubs
 
 struct Counters {
     unsigned long long cursor;        // scratch cursor
@@ -53,6 +54,7 @@ struct Counters {
     uint32_t q[NQ];
     unsigned long long q_cand[NQ];    // candidates per class
     unsigned long long q_deg[NQ];     // neighbour-list entries read per class
+    uint32_t bm_next;                 // bitmap kernel work counter (hubs, then the rest)
 };
 
 __device__ __forceinline__ uint32_t next_pow2(uint32_t v) {
@@ -119,7 +121,7 @@ __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
                 q = c <= (unsigned long long)M_CAP ? Q_MERGE : Q_MERGE2;
                 ub = c;
             } else if (heavy || (c > (unsigned long long)W2_CAP && dg > 1)) {
-                q = Q_BITMAP;
+                q = (dg >= BM_WARP_PER_LIST || c >= (unsigned long long)HUB_CAND) ? Q_HUB : Q_BITMAP;
                 ub = c + (heavy ? (unsigned long long)w : 0ull);
                 if (ub > (unsigned long long)nz) ub = (unsigned long long)nz;
             } else if (c > 0 && rxoff[a + 1] - rxoff[a] == 1) {
@@ -307,9 +309,10 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
 // ------------------------------------------------------------ bucket class
 // One warp per light x with W_CAP < c <= CAP, deduplicated by an
 // order-preserving bucket sort: pass 1 counts the candidates per bucket of
-// the z domain (bucket = z * nb / nz, monotone in z), pass 2 scatters them to
-// their bucket's range, then every lane sorts and deduplicates whole buckets
-// (about 8 values each) by insertion, and the buckets are written in order.
+// the z domain (bucket = z >> sh with (nz - 1) >> sh < nb, monotone in z),
+// pass 2 scatters them to their bucket's range, then every lane sorts and
+// deduplicates whole buckets (about 8 values each) by insertion, and the
+// buckets are written in order.
 // Work is linear in c; no block-wide synchronisation is needed.
 template <int CAP, int NB>
 __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Counters* qc,
@@ -333,6 +336,8 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
             continue;
         }
         const uint32_t nb = min((uint32_t)NB, max(32u, next_pow2((n + 7) / 8)));
+        // bucket = z >> sh: monotone in z, and ((nz - 1) >> sh) < nb
+        const int sh = max(0, (32 - __clz((uint32_t)(nz - 1))) - (31 - __clz(nb)));
         for (uint32_t k = lane; k < NB; k += 32) cnt[k] = 0;
         __syncwarp();
         const int32_t e0 = A.rxoff[a], e1 = A.rxoff[a + 1];
@@ -347,7 +352,7 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (zz[u] != 0xffffffffu)
-                        atomicAdd(&cnt[(uint32_t)(((uint64_t)zz[u] * nb) / nz)], 1u);
+                        atomicAdd(&cnt[zz[u] >> sh], 1u);
             }
         }
         __syncwarp();
@@ -378,7 +383,7 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (zz[u] != 0xffffffffu) {
-                        const uint32_t p = atomicAdd(&cur[(uint32_t)(((uint64_t)zz[u] * nb) / nz)], 1u);
+                        const uint32_t p = atomicAdd(&cur[zz[u] >> sh], 1u);
                         buf[p] = (int32_t)zz[u];
                     }
             }
@@ -523,8 +528,10 @@ __global__ void __launch_bounds__(M_THREADS)
         if (tid == 0) s_base = atomicAdd(&A.ctr->cursor, (unsigned long long)c);
         int32_t* src = dyn_m;
         int32_t* dst = dyn_m + CAP;
-        // gather: flat candidate f of run k is S[b_k][f - run_k]
+        // gather: flat candidate f of run k is S[b_k][f - run_k]; a thread's f
+        // only grow, so its run index k only moves forward
         constexpr int U = 8;
+        int k = 0;
         for (int32_t f0 = tid; f0 < c; f0 += U * M_THREADS) {
             int32_t zz[U];
 #pragma unroll
@@ -532,12 +539,8 @@ __global__ void __launch_bounds__(M_THREADS)
                 const int32_t f = f0 + u * M_THREADS;
                 zz[u] = 0;
                 if (f < c) {
-                    int32_t lo = 0, hi = deg;    // last k with s_runs[0][k] <= f
-                    while (hi - lo > 1) {
-                        const int32_t mid = (lo + hi) >> 1;
-                        if (s_runs[0][mid] <= f) lo = mid; else hi = mid;
-                    }
-                    zz[u] = A.szcol[s_start[lo] + (f - s_runs[0][lo])];
+                    while (s_runs[0][k + 1] <= f) ++k;
+                    zz[u] = A.szcol[s_start[k] + (f - s_runs[0][k])];
                 }
             }
 #pragma unroll
@@ -636,7 +639,8 @@ __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, int32_t r) {
 // Persistent blocks, one x at a time.  The bitmap and its summary start at
 // zero and are cleared word by word as they are emitted.
 __global__ void __launch_bounds__(BM_THREADS, 1)
-    light_bitmap_kernel(LightArgs A, const int32_t* queue, const Counters* qc, int32_t win_words) {
+    light_bitmap_kernel(LightArgs A, const int32_t* hub_queue, const int32_t* queue,
+                        const Counters* qc, int32_t win_words) {
     extern __shared__ uint32_t smem_bm[];
     uint32_t* bm = smem_bm;                       // win_words
     uint32_t* summ = smem_bm + win_words;         // win_words / 32
@@ -644,12 +648,20 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_pre[BM_THREADS];     // prefix of the neighbour list lengths
     __shared__ int32_t s_start[BM_THREADS];    // list start (negative: in slcol)
-    const uint32_t nq = qc->q[Q_BITMAP];
+    __shared__ uint32_t s_item[2];             // work items of this row and the next
+    const uint32_t nh = qc->q[Q_HUB], nq = nh + qc->q[Q_BITMAP];
     const int64_t win_bits = (int64_t)win_words * 32;
     for (int32_t i = threadIdx.x; i < win_words + win_words / 32; i += blockDim.x) smem_bm[i] = 0;
+    // rows are taken from a global counter, hubs first (longest work first);
+    // the next row's item is fetched while this one is processed, into the
+    // other slot of s_item
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(&A.ctr->bm_next, 1u);
     __syncthreads();
-    for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
-        const int32_t a = queue[qi];
+    for (uint32_t r = 0;; ++r) {
+        const uint32_t qi = s_item[r & 1];
+        if (qi >= nq) break;
+        if (threadIdx.x == 0) s_item[(r + 1) & 1] = atomicAdd(&A.ctr->bm_next, 1u);
+        const int32_t a = qi < nh ? hub_queue[qi] : queue[qi - nh];
         const int32_t h = A.hx[a];
         const bool heavy = h >= 0;
         const int32_t e0 = A.rxoff[a], deg = A.rxoff[a + 1] - e0;
@@ -666,28 +678,53 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
             const int64_t zend = min(A.nz, z0 + win_bits);
             const int32_t nwords = (int32_t)((zend - z0 + 31) >> 5);
             const int32_t nsumm = (nwords + 31) >> 5;
-            // rows with many neighbours (the hubs): one warp per neighbour list,
-            // lanes over the list, no search needed
+            // rows with many neighbours (the hubs): each warp takes 32 neighbour
+            // lists at a time, its lanes read the 32 lists' bounds at once, and
+            // the warp walks their candidates flat (lane l takes flat
+            // candidates l, l + 32, ...; the owning list is found by a binary
+            // search over the lanes' prefix sums with shuffles)
             if (deg >= BM_WARP_PER_LIST) {
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                for (int32_t t = warp; t < deg; t += BM_THREADS / 32) {
-                    const int32_t b = A.rycol[e0 + t];
-                    const int32_t j = heavy ? A.hy[b] : -1;
-                    const int32_t* list;
-                    int32_t L;
-                    if (j >= 0) {
-                        list = A.slcol + A.sloff[j];
-                        L = A.sloff[j + 1] - A.sloff[j];
-                    } else {
-                        list = A.szcol + A.syoff[b];
-                        L = A.syoff[b + 1] - A.syoff[b];
+                for (int32_t t0 = warp * 32; t0 < deg; t0 += BM_THREADS) {
+                    int32_t start = 0, L = 0;   // start < 0: -(offset in slcol) - 1
+                    if (t0 + lane < deg) {
+                        const int32_t b = A.rycol[e0 + t0 + lane];
+                        const int32_t j = heavy ? A.hy[b] : -1;
+                        if (j >= 0) {
+                            start = -A.sloff[j] - 1;
+                            L = A.sloff[j + 1] - A.sloff[j];
+                        } else {
+                            start = A.syoff[b];
+                            L = A.syoff[b + 1] - start;
+                        }
                     }
-                    for (int32_t q0 = lane; q0 < L; q0 += 128) {
-                        int32_t zz[4];
+                    int32_t incl = L;
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) zz[u] = (q0 + 32 * u < L) ? list[q0 + 32 * u] : -1;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int32_t excl = incl - L;
+                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    constexpr int UH = 4;
+                    for (int32_t f0 = 0; f0 < total; f0 += 32 * UH) {
+                        int32_t zz[UH];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
+                        for (int u = 0; u < UH; ++u) {
+                            const int32_t f = f0 + 32 * u + lane;
+                            int owner = 0;              // last lane with excl <= f
+#pragma unroll
+                            for (int step = 16; step > 0; step >>= 1) {
+                                const int32_t e = __shfl_sync(0xffffffffu, excl, owner + step);
+                                if (e <= f) owner += step;
+                            }
+                            const int32_t st = __shfl_sync(0xffffffffu, start, owner);
+                            const int32_t off = f - __shfl_sync(0xffffffffu, excl, owner);
+                            zz[u] = -1;
+                            if (f < total) zz[u] = st >= 0 ? A.szcol[st + off] : A.slcol[-st - 1 + off];
+                        }
+#pragma unroll
+                        for (int u = 0; u < UH; ++u)
                             if (zz[u] >= z0 && zz[u] < zend) mark(bm, summ, (int32_t)(zz[u] - z0));
                     }
                 }
@@ -908,7 +945,7 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         }
         tend(TM_LIGHT_MERGE);
     }
-    if (hc.q[Q_BITMAP]) {
+    if (hc.q[Q_BITMAP] + hc.q[Q_HUB]) {
         int64_t words = (g.nz + 31) / 32;
         int32_t win = (int32_t)std::min<int64_t>(words, BM_MAX_WORDS);
         win = (win + 1023) & ~1023;                 // whole summary words
@@ -921,8 +958,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
             attrb = true;
         }
         tbegin(TM_LIGHT_BITMAP);
-        light_bitmap_kernel<<<grid_for(hc.q[Q_BITMAP], 1, 152), BM_THREADS, sm, st>>>(
-            A, queues + (int64_t)Q_BITMAP * nx, ctr, win);
+        light_bitmap_kernel<<<grid_for(hc.q[Q_BITMAP] + hc.q[Q_HUB], 1, 152), BM_THREADS, sm, st>>>(
+            A, queues + (int64_t)Q_HUB * nx, queues + (int64_t)Q_BITMAP * nx, ctr, win);
         JP_CHECK_LAUNCH();
         tend(TM_LIGHT_BITMAP);
     }
