@@ -161,8 +161,14 @@ void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t s
                 void* (*get_encode)());
 
 // Light part + union (jp_light.cu)
+// A row's list: tmp_off >= 0 is its offset in tmp, holding z values, or, with
+// TMP_IDS set, z ids (bitmap rows); tmp_off < 0 is -(offset in szval) - 1 for
+// a row with a single neighbour list, read in place.
+constexpr int64_t TMP_IDS = (int64_t)1 << 62;
+
 struct LightResult {
     int64_t* tmp_off = nullptr;   // [nx]
+    int32_t* szval = nullptr;     // [ns] zval[szcol]
     int32_t* cnt = nullptr;       // [nx]
     int32_t* tmp = nullptr;
     int64_t tmp_cap = 0;

@@ -27,7 +27,10 @@
 //                 the heavy product bitmap G: this is the union with the
 //                 matrix part.  Set bits are emitted in z order.
 // Each x's sorted distinct list goes to a scratch buffer at an offset taken
-// by one atomic add; the output pass then places the lists in x order.
+// by one atomic add; the output pass then places the lists in x order.  The
+// sort and merge classes read the lists of S as z values (szval, in id
+// order, which is value order) and write values; the bitmap class marks and
+// writes z ids, which the output pass maps to values.
 #include "jp_internal.cuh"
 
 namespace jp {
@@ -55,6 +58,7 @@ struct Counters {
     unsigned long long q_cand[NQ];    // candidates per class
     unsigned long long q_deg[NQ];     // neighbour-list entries read per class
     uint32_t bm_next;                 // bitmap kernel work counter (hubs, then the rest)
+    int32_t vmin, vmax;               // smallest and largest z value
 };
 
 __device__ __forceinline__ uint32_t next_pow2(uint32_t v) {
@@ -97,7 +101,7 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // Thread per x: class, queue slot (warp-aggregated atomics), block-aggregated sums.
 // A light x with a single neighbour list needs no deduplication: S[b] is
 // sorted and distinct, so the output pass reads it in place (tmp_off holds
-// -(offset in szcol) - 1) and no scratch is used.
+// -(offset in szval) - 1) and no scratch is used.
 __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
                              const int32_t* rxoff, const int32_t* rycol, const int32_t* syoff,
                              int64_t w, int64_t nz, int32_t* queues, int32_t* cnt,
@@ -228,6 +232,9 @@ struct LightArgs {
     const int32_t* rycol;
     const int32_t* syoff;
     const int32_t* szcol;
+    const int32_t* szval;      // zval[szcol]: the lists of S as z values (same order)
+    int32_t vmin;              // smallest z value
+    uint32_t vspan;            // largest minus smallest z value
     const int32_t* deg_sy;
     const int32_t* hx;
     const int32_t* hy;
@@ -267,7 +274,7 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], len = A.syoff[b + 1] - s0;
             for (int32_t t = lane; t < len; t += 32)
-                if (off + t < CAP) keys[off + t] = A.szcol[s0 + t];
+                if (off + t < CAP) keys[off + t] = A.szval[s0 + t];
             off += len;
         }
         if (off > CAP) {  // cannot happen: the class bound is the candidate count
@@ -309,7 +316,7 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
 // ------------------------------------------------------------ bucket class
 // One warp per light x with W_CAP < c <= CAP, deduplicated by an
 // order-preserving bucket sort: pass 1 counts the candidates per bucket of
-// the z domain (bucket = z >> sh with (nz - 1) >> sh < nb, monotone in z),
+// the z values (bucket = (z - vmin) >> sh with vspan >> sh < nb, monotone),
 // pass 2 scatters them to their bucket's range, then every lane sorts and
 // deduplicates whole buckets (about 8 values each) by insertion, and the
 // buckets are written in order.
@@ -324,7 +331,6 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
     uint32_t* cnt = reinterpret_cast<uint32_t*>(buf + CAP);   // per-bucket count, later distinct
     uint32_t* cur = cnt + NB;                                 // per-bucket cursor / end
     const uint32_t nq = qc->q[qid];
-    const uint64_t nz = (uint64_t)A.nz;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     constexpr int PER = NB / 32;                              // counters per lane in scans
@@ -336,8 +342,8 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
             continue;
         }
         const uint32_t nb = min((uint32_t)NB, max(32u, next_pow2((n + 7) / 8)));
-        // bucket = z >> sh: monotone in z, and ((nz - 1) >> sh) < nb
-        const int sh = max(0, (32 - __clz((uint32_t)(nz - 1))) - (31 - __clz(nb)));
+        // bucket = (z - vmin) >> sh: monotone in z, and (vspan >> sh) < nb
+        const int sh = max(0, (32 - __clz(A.vspan)) - (31 - __clz(nb)));
         for (uint32_t k = lane; k < NB; k += 32) cnt[k] = 0;
         __syncwarp();
         const int32_t e0 = A.rxoff[a], e1 = A.rxoff[a + 1];
@@ -345,14 +351,12 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
             for (int32_t t0 = lane; t0 < L; t0 += 128) {
-                uint32_t zz[4];
+                int32_t zz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) zz[u] = (t0 + 32 * u < L) ? A.szval[s0 + t0 + 32 * u] : 0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    zz[u] = (t0 + 32 * u < L) ? (uint32_t)A.szcol[s0 + t0 + 32 * u] : 0xffffffffu;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (zz[u] != 0xffffffffu)
-                        atomicAdd(&cnt[zz[u] >> sh], 1u);
+                    if (t0 + 32 * u < L) atomicAdd(&cnt[(uint32_t)(zz[u] - A.vmin) >> sh], 1u);
             }
         }
         __syncwarp();
@@ -376,15 +380,14 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
             for (int32_t t0 = lane; t0 < L; t0 += 128) {
-                uint32_t zz[4];
+                int32_t zz[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) zz[u] = (t0 + 32 * u < L) ? A.szval[s0 + t0 + 32 * u] : 0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    zz[u] = (t0 + 32 * u < L) ? (uint32_t)A.szcol[s0 + t0 + 32 * u] : 0xffffffffu;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (zz[u] != 0xffffffffu) {
-                        const uint32_t p = atomicAdd(&cur[zz[u] >> sh], 1u);
-                        buf[p] = (int32_t)zz[u];
+                    if (t0 + 32 * u < L) {
+                        const uint32_t p = atomicAdd(&cur[(uint32_t)(zz[u] - A.vmin) >> sh], 1u);
+                        buf[p] = zz[u];
                     }
             }
         }
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(M_THREADS)
     light_merge_kernel(LightArgs A, const int32_t* queue, const Counters* qc, int qid) {
     extern __shared__ int32_t dyn_m[];
     __shared__ int32_t s_runs[2][M_MAXL + 1];   // run boundaries, current and next level
-    __shared__ int32_t s_start[M_MAXL];         // list starts in szcol
+    __shared__ int32_t s_start[M_MAXL];         // list starts in szval
     __shared__ uint32_t s_wsum[M_THREADS / 32];
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -540,7 +543,7 @@ __global__ void __launch_bounds__(M_THREADS)
                 zz[u] = 0;
                 if (f < c) {
                     while (s_runs[0][k + 1] <= f) ++k;
-                    zz[u] = A.szcol[s_start[k] + (f - s_runs[0][k])];
+                    zz[u] = A.szval[s_start[k] + (f - s_runs[0][k])];
                 }
             }
 #pragma unroll
@@ -570,16 +573,17 @@ __global__ void __launch_bounds__(M_THREADS)
                 const int32_t seg_end = min(o_end, b1);
                 const int32_t i = co_rank(src + a0, a1 - a0, src + a1, b1 - a1, o - a0);
                 int32_t ia = a0 + i, ib = a1 + (o - a0 - i);
-                int32_t va = ia < a1 ? src[ia] : INT32_MAX;
-                int32_t vb = ib < b1 ? src[ib] : INT32_MAX;
-                for (; o < seg_end; ++o) {       // z ids are below INT32_MAX
-                    // branch-free step: one shared-memory load per output
-                    const bool ta = va <= vb;
+                int32_t va = ia < a1 ? src[ia] : 0;
+                int32_t vb = ib < b1 ? src[ib] : 0;
+                for (; o < seg_end; ++o) {
+                    // branch-free step: one shared-memory load per output; take A
+                    // while it has values and (B is done or A's head is not larger)
+                    const bool ta = ia < a1 && (ib >= b1 || va <= vb);
                     dst[o] = ta ? va : vb;
                     ia += ta;
                     ib += !ta;
                     const int32_t ni = ta ? ia : ib;
-                    const int32_t nv = ni < (ta ? a1 : b1) ? src[ni] : INT32_MAX;
+                    const int32_t nv = ni < (ta ? a1 : b1) ? src[ni] : 0;
                     va = ta ? nv : va;
                     vb = ta ? vb : nv;
                 }
@@ -838,9 +842,16 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
         if (threadIdx.x == 0) {
             if (running > ub) atomicOr(A.status, ST_BADINDEX);
             A.cnt[a] = room ? (int32_t)min(running, ub) : 0;
-            A.tmp_off[a] = (int64_t)base;
+            A.tmp_off[a] = (int64_t)base | TMP_IDS;   // this list holds z ids
         }
     }
+}
+
+__global__ void szval_kernel(const int32_t* __restrict__ szcol, const int32_t* __restrict__ zval,
+                             int64_t n, int32_t* __restrict__ szval) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        szval[i] = zval[szcol[i]];
 }
 
 }  // namespace
@@ -866,6 +877,11 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         nx, cand, p.hx, g.rxoff, g.rycol, g.syoff, p.w, g.nz, queues, lr.cnt, lr.tmp_off, ctr);
     JP_CHECK_LAUNCH();
     tend(TM_CLASSIFY);
+    if (g.nz > 0) {   // z ids are in value order: the first and last are the extremes
+        JP_CUDA_TRY(cudaMemcpyAsync(&ctr->vmin, g.zval, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        JP_CUDA_TRY(cudaMemcpyAsync(&ctr->vmax, g.zval + g.nz - 1, sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, st));
+    }
     Counters hc;
     JP_CUDA_TRY(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     JP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -877,12 +893,23 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     }
     lr.tmp_cap = (int64_t)hc.need;
     lr.tmp = ws.get<int32_t>((size_t)(lr.tmp_cap + 1));
+    // the lists of S as z values: the sort and merge classes work on values
+    // (ids are assigned in value order, so the order and the distinct sets
+    // are the same) and write them, so output placement maps only bitmap rows
+    lr.szval = ws.get<int32_t>((size_t)g.ns + 1);
+    if (g.ns > 0) {
+        szval_kernel<<<grid_for(g.ns, 256, 152 * 8), 256, 0, st>>>(g.szcol, g.zval, g.ns, lr.szval);
+        JP_CHECK_LAUNCH();
+    }
 
     LightArgs A;
     A.rxoff = g.rxoff;
     A.rycol = g.rycol;
     A.syoff = g.syoff;
     A.szcol = g.szcol;
+    A.szval = lr.szval;
+    A.vmin = hc.vmin;
+    A.vspan = (uint32_t)hc.vmax - (uint32_t)hc.vmin;
     A.deg_sy = g.deg_sy;
     A.hx = p.hx;
     A.hy = p.hy;

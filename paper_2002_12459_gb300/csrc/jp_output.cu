@@ -1,6 +1,7 @@
 // Output placement (the final union pass of Algorithm 1): every x's sorted
 // distinct z list is moved from the scratch buffer to its place in the
-// globally sorted result, and ids are mapped back to int32 values.
+// globally sorted result; the lists of bitmap rows hold z ids, which are
+// mapped to values here (the other lists already hold values).
 //
 // Because x ids and z ids are assigned in value order, writing the lists in
 // x-id order with each list in z-id order gives the lexicographic order of
@@ -33,11 +34,16 @@ __device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_
     return lo;
 }
 
-// A row's list lives in the scratch buffer (tmp_off >= 0) or, for rows with a
-// single neighbour list, in place in szcol (tmp_off = -(offset) - 1).
-__device__ __forceinline__ int32_t list_at(const int32_t* tmp, const int32_t* szcol, int64_t toff,
-                                           int64_t i) {
-    return toff >= 0 ? tmp[toff + i] : szcol[-toff - 1 + i];
+// Entry i of a row's list (see TMP_IDS): a z value read from tmp or in place
+// from szval, or, for bitmap rows, a z id (*is_id set) to be mapped by zval.
+__device__ __forceinline__ int32_t list_at(const int32_t* tmp, const int32_t* szval, int64_t toff,
+                                           int64_t i, bool* is_id) {
+    if (toff < 0) {
+        *is_id = false;
+        return szval[-toff - 1 + i];
+    }
+    *is_id = (toff & TMP_IDS) != 0;
+    return tmp[(toff & ~TMP_IDS) + i];
 }
 
 // tile_x[t] = the x whose output range holds output t * tile (thread per x:
@@ -59,7 +65,7 @@ __global__ void tile_start_kernel(const int64_t* __restrict__ out_off, int64_t n
 __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int32_t* __restrict__ tile_x,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
-                             const int32_t* __restrict__ szcol,
+                             const int32_t* __restrict__ szval,
                              const int32_t* __restrict__ xval, const int32_t* __restrict__ xval2,
                              const int32_t* __restrict__ zval, int64_t count,
                              int32_t* __restrict__ out_x, int32_t* __restrict__ out_x2,
@@ -88,30 +94,33 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
     __syncthreads();
     // all of a thread's list reads, then all of its id -> value gathers, then
     // the stores: OUT_VT independent loads in flight per phase
-    int32_t zid[OUT_VT], xv[OUT_VT], xv2[OUT_VT];
+    int32_t zv[OUT_VT], xv[OUT_VT], xv2[OUT_VT];
+    uint32_t ids = 0;   // bit k: zv[k] is a z id
 #pragma unroll
     for (int k = 0; k < OUT_VT; ++k) {
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
-        zid[k] = -1;
+        zv[k] = 0;
         xv[k] = 0;
         xv2[k] = 0;
+        bool is_id = false;
         if (o <= o_last) {
             if (staged) {
                 const int64_t i = find_x(s_off, 0, nxs, o);
-                zid[k] = list_at(tmp, szcol, s_toff[i], o - s_off[i]);
+                zv[k] = list_at(tmp, szval, s_toff[i], o - s_off[i], &is_id);
                 xv[k] = s_xv[i];
                 if (xval2) xv2[k] = s_xv2[i];
             } else {
                 const int64_t x = find_x(out_off, xlo, xhi, o);
-                zid[k] = list_at(tmp, szcol, tmp_off[x], o - out_off[x]);
+                zv[k] = list_at(tmp, szval, tmp_off[x], o - out_off[x], &is_id);
                 xv[k] = xval[x];
                 if (xval2) xv2[k] = xval2[x];
             }
         }
+        ids |= (uint32_t)is_id << k;
     }
-    int32_t zv[OUT_VT];
 #pragma unroll
-    for (int k = 0; k < OUT_VT; ++k) zv[k] = zid[k] >= 0 ? zval[zid[k]] : 0;
+    for (int k = 0; k < OUT_VT; ++k)
+        if (ids >> k & 1u) zv[k] = zval[zv[k]];
 #pragma unroll
     for (int k = 0; k < OUT_VT; ++k) {
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
@@ -162,7 +171,7 @@ void output_write_rows(const Graph& g, const LightResult& lr, const int64_t* out
     const int64_t per_block = (int64_t)OUT_THREADS * OUT_VT;
     const int64_t blocks = (count + per_block - 1) / per_block;
     place_kernel<<<(unsigned)blocks, OUT_THREADS, 0, st>>>(out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp,
-                                                          g.szcol, rowval, rowval2, g.zval, count,
+                                                          lr.szval, rowval, rowval2, g.zval, count,
                                                           out_row, out_row2, out_z);
     JP_CHECK_LAUNCH();
 }

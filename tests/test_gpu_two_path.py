@@ -186,8 +186,11 @@ def _class_relation(seed):
     have = np.bincount(ry, minlength=ny)
     extra_y = np.repeat(np.arange(ny), np.maximum(ydeg - have, 0))
     extra_x = nx + np.arange(len(extra_y))
-    return (np.concatenate([rx, extra_x.astype(np.int32)]),
-            np.concatenate([ry, extra_y.astype(np.int32)]))
+    rx = np.concatenate([rx, extra_x]).astype(np.int64)
+    # x -> x * 2654435761 + 12345 (mod 2^32, as int32) is one-to-one: values spread
+    # over the whole signed range, in an order unrelated to the draw order
+    rx = ((rx * 2654435761 + 12345) & 0xFFFFFFFF).astype(np.uint32).view(np.int32)
+    return rx, np.concatenate([ry, extra_y.astype(np.int32)])
 
 
 @pytest.mark.parametrize("seed", range(2))
