@@ -74,21 +74,57 @@ __device__ __forceinline__ int64_t cand_of(int32_t b, bool heavy, const int32_t*
     return deg_sy[b];
 }
 
-// Warp per x: candidate count c(x).
+// Candidate count c(x): lane per x, each lane summing its own lists; the x
+// of a warp with more than 32 lists are then summed by the whole warp, one
+// after another.
 __global__ void cand_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
                             const int32_t* hx, const int32_t* hy, const int32_t* sloff,
                             const int32_t* deg_sy, int64_t* cand) {
     const int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = warp; a < nx; a += nwarps) {
-        const bool heavy = hx[a] >= 0;
-        unsigned long long c = 0;
-        for (int32_t e = rxoff[a] + lane; e < rxoff[a + 1]; e += 32)
-            c += (unsigned long long)cand_of(rycol[e], heavy, hy, sloff, deg_sy);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < nx;
+         base += stride) {
+        const int64_t a = base + lane;
+        const bool valid = a < nx;
+        int32_t e0 = 0, e1 = 0;
+        bool heavy = false;
+        if (valid) {
+            e0 = rxoff[a];
+            e1 = rxoff[a + 1];
+            heavy = hx[a] >= 0;
+        }
+        const bool small = valid && e1 - e0 <= 32;
+        long long c = 0;
+        if (small) {
+            int32_t e = e0;
+            for (; e + 4 <= e1; e += 4) {        // four independent gathers in flight
+                const int32_t b0 = rycol[e], b1 = rycol[e + 1], b2 = rycol[e + 2], b3 = rycol[e + 3];
+                c += cand_of(b0, heavy, hy, sloff, deg_sy) + cand_of(b1, heavy, hy, sloff, deg_sy) +
+                     cand_of(b2, heavy, hy, sloff, deg_sy) + cand_of(b3, heavy, hy, sloff, deg_sy);
+            }
+            for (; e < e1; ++e) c += cand_of(rycol[e], heavy, hy, sloff, deg_sy);
+        }
+        unsigned big = __ballot_sync(0xffffffffu, valid && !small);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t f0 = __shfl_sync(0xffffffffu, e0, j), f1 = __shfl_sync(0xffffffffu, e1, j);
+            const bool hj = __shfl_sync(0xffffffffu, heavy, j);
+            long long sj = 0;
+            int32_t e = f0 + lane;
+            for (; e + 7 * 32 < f1; e += 8 * 32) {   // eight independent chains per lane
+                int32_t b[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-        if (lane == 0) cand[a] = (int64_t)c;
+                for (int u = 0; u < 8; ++u) b[u] = rycol[e + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sj += cand_of(b[u], hj, hy, sloff, deg_sy);
+            }
+            for (; e < f1; e += 32) sj += cand_of(rycol[e], hj, hy, sloff, deg_sy);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+            if (lane == j) c = sj;
+        }
+        if (valid) cand[a] = (int64_t)c;
     }
 }
 
@@ -870,7 +906,7 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     Counters* ctr = ws.get<Counters>(1);
     JP_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     tbegin(TM_CLASSIFY);
-    cand_kernel<<<grid_for(nx * 32, 256, 152 * 16), 256, 0, st>>>(
+    cand_kernel<<<grid_for(nx, 256, 152 * 16), 256, 0, st>>>(
         nx, g.rxoff, g.rycol, p.hx, p.hy, p.sloff, g.deg_sy, cand);
     JP_CHECK_LAUNCH();
     queue_kernel<<<grid_for(nx, 256, 152 * 8), 256, 0, st>>>(

@@ -62,7 +62,10 @@ __global__ void tile_start_kernel(const int64_t* __restrict__ out_off, int64_t n
 // tile's x range is short its offsets are staged in shared memory.  Thread t
 // writes outputs o0 + t + k*OUT_THREADS, so each store instruction of a warp
 // covers 32 consecutive outputs.
-__global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
+// X2: a second row column (the star's x2) is written next to the first.
+template <bool X2>
+__global__ void __launch_bounds__(OUT_THREADS)
+    place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int32_t* __restrict__ tile_x,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
                              const int32_t* __restrict__ szval,
@@ -87,7 +90,7 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
             s_off[i] = out_off[xlo + i];
             s_toff[i] = tmp_off[xlo + i];
             s_xv[i] = xval[xlo + i];
-            if (xval2) s_xv2[i] = xval2[xlo + i];
+            if (X2) s_xv2[i] = xval2[xlo + i];
         }
         if (threadIdx.x == 0) s_off[nxs] = (xhi < nx) ? out_off[xhi] : count;
     }
@@ -108,12 +111,12 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                 const int64_t i = find_x(s_off, 0, nxs, o);
                 zv[k] = list_at(tmp, szval, s_toff[i], o - s_off[i], &is_id);
                 xv[k] = s_xv[i];
-                if (xval2) xv2[k] = s_xv2[i];
+                if (X2) xv2[k] = s_xv2[i];
             } else {
                 const int64_t x = find_x(out_off, xlo, xhi, o);
                 zv[k] = list_at(tmp, szval, tmp_off[x], o - out_off[x], &is_id);
                 xv[k] = xval[x];
-                if (xval2) xv2[k] = xval2[x];
+                if (X2) xv2[k] = xval2[x];
             }
         }
         ids |= (uint32_t)is_id << k;
@@ -126,7 +129,7 @@ __global__ void place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
         if (o <= o_last) {
             out_x[o] = xv[k];
-            if (out_x2) out_x2[o] = xv2[k];
+            if (X2) out_x2[o] = xv2[k];
             out_z[o] = zv[k];
         }
     }
@@ -170,9 +173,14 @@ void output_write_rows(const Graph& g, const LightResult& lr, const int64_t* out
     if (count <= 0) return;
     const int64_t per_block = (int64_t)OUT_THREADS * OUT_VT;
     const int64_t blocks = (count + per_block - 1) / per_block;
-    place_kernel<<<(unsigned)blocks, OUT_THREADS, 0, st>>>(out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp,
-                                                          lr.szval, rowval, rowval2, g.zval, count,
-                                                          out_row, out_row2, out_z);
+    if (rowval2 && out_row2)
+        place_kernel<true><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
+            out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp, lr.szval, rowval, rowval2, g.zval, count,
+            out_row, out_row2, out_z);
+    else
+        place_kernel<false><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
+            out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp, lr.szval, rowval, nullptr, g.zval, count,
+            out_row, nullptr, out_z);
     JP_CHECK_LAUNCH();
 }
 
