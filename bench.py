@@ -192,6 +192,52 @@ def roofline(st, peaks, peak_kind, ms_by_slot):
     return top, per
 
 
+# ----------------------------------------------------------------- learned thresholds
+def learned_vs_cost_model(ctx, dx, dy, flush, cost_ms, st_cost, args):
+    """Query time at the shipped predictor's thresholds (JP_LEARNED) next to
+    the cost-model time just measured, plus the held-out summary written when
+    the predictor was trained."""
+    import torch
+    from paper_2002_12459_gb300 import jp
+    pred = jp.Predictor.trained(0)
+    ctx.set_predictor(pred)
+    ctx.set_threshold("learned")
+    ms, st = [], None
+    try:
+        for i in range(1 + args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(ctx.stream)
+            ox, oz = ctx.two_path(dx, dy)
+            ev1.record(ctx.stream)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            if i > 0:
+                ms.append(ev0.elapsed_time(ev1))
+            del ox, oz
+    finally:
+        ctx.set_predictor(None)
+        ctx.set_threshold(args.mode, args.delta1, args.delta2)
+        pred.close()
+    lm = sum(ms) / len(ms)
+    log(f"[bench] learned thresholds {st['delta1']},{st['delta2']}: {lm:.2f} ms "
+        f"(cost model {st_cost['delta1']},{st_cost['delta2']}: {cost_ms:.2f} ms)")
+    held = None
+    rep = os.path.join(ROOT, "paper_2002_12459_gb300", "predictor", "report.json")
+    if os.path.exists(rep):
+        with open(rep) as f:
+            held = json.load(f)["summary"]
+    return {"cost_model_ms": cost_ms, "learned_ms": lm, "learned_over_cost_model": lm / cost_ms,
+            "cost_model_delta": [st_cost["delta1"], st_cost["delta2"]],
+            "learned_delta": [st["delta1"], st["delta2"]],
+            "out_count_equal": st["out_count"] == st_cost["out_count"],
+            "held_out": None if held is None else {
+                k: held[k] for k in ("relations", "learned_over_best_geomean",
+                                     "cost_over_best_geomean", "train_relations")}}
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -248,6 +294,12 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
+
+    # the same query at the learned thresholds (the shipped predictor), timed
+    # the same way, against the cost-model thresholds above
+    learned = None
+    if rank == 0 and not args.no_learned and args.mode == "cost_model":
+        learned = learned_vs_cost_model(ctx, dx, dy, flush, mean_ms, st, args)
 
     # sampled bit-exact check of the last result against the per-row oracle
     parity = None
@@ -315,7 +367,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "256 MiB flush written before every step",
                    "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
         "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "parity": parity,
+        "clocks": clocks, "parity": parity, "learned_vs_cost_model": learned,
     }
 
 
@@ -448,6 +500,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip timing the query at the shipped predictor's thresholds")
     ap.add_argument("--ref-cand", type=float, default=1.5e7)
     args = ap.parse_args()
 

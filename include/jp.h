@@ -57,7 +57,9 @@ extern "C" {
 #define JP_FIXED        0    /* use the given Delta1, Delta2 (clamped to [1, N]) */
 #define JP_CLOSED_FORM  1    /* Lemma 3's minimiser of the omega = 2 cost, with the Section 5 output estimate */
 #define JP_COST_MODEL   2    /* Algorithm 3 (Section 5) with GPU-calibrated constants */
-#define JP_LEARNED      3    /* thresholds predicted by the model set with jp_set_predictor */
+#define JP_LEARNED      3    /* thresholds predicted by the model set with jp_set_predictor,
+                                kept unless the cost model (Algorithm 3's) prices them above
+                                3 x its own choice, which is then used instead */
 
 typedef struct jp_ctx jp_ctx;
 
@@ -107,6 +109,9 @@ typedef struct {
                                   classification, 6-9 light kernels (warp sort,
                                   bucket sort, merge, bitmap+union), 10 output count,
                                   11 output placement kernel, 12 whole query */
+    int64_t learned_judged;    /* JP_LEARNED only: 1 the model's thresholds were used, 2 the cost
+                                  model judged them too costly (modelled cost above 3 x that of
+                                  Algorithm 3's thresholds) and Algorithm 3's were used; else 0 */
 } jp_stats;
 
 typedef void* (*jp_alloc_fn)(size_t bytes, void* stream, void* user);

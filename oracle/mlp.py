@@ -2,9 +2,12 @@
 
 The predictor maps a relation's degree distribution to thresholds
 (log Delta1, log Delta2).  Its features are two 64-bin log-degree histograms
-(x degrees and y degrees), each bin holding the fraction of values whose
-degree d has  bin(d) = min(63, floor(4 * log2 d)) = min(63, floor(log2 d^4)),
-computed exactly here with Python integers.  The network is a plain MLP
+(x degrees and y degrees): bin(d) = min(63, floor(4 * log2 d)) =
+min(63, floor(log2 d^4)), computed exactly here with Python integers, and
+each bin's count c enters as log2(1 + c) / 32, which keeps the relation's
+scale (a relation twice as large moves every populated bin up by about 1/32;
+fractions of the domain would hide it, while the best thresholds grow with N,
+Lemma 3).  The network is a plain MLP
 128 -> 256 -> 256 -> 2 with ReLU, weights rounded to bfloat16 and all
 arithmetic in float64.  The backward pass is the chain rule of that forward
 pass written out; it is pinned against finite differences in the tests.
@@ -25,16 +28,21 @@ def log_degree_bin(d: int) -> int:
 
 
 def histogram(degrees) -> np.ndarray:
-    """64-bin log-degree histogram as fractions of the values with degree >= 1."""
+    """64-bin log-degree histogram: the number of values with degree >= 1 per bin."""
     h = np.zeros(NBIN, np.float64)
-    ds = [int(d) for d in degrees if d >= 1]
-    for d in ds:
-        h[log_degree_bin(d)] += 1
-    return h / max(len(ds), 1)
+    for d in degrees:
+        if int(d) >= 1:
+            h[log_degree_bin(int(d))] += 1
+    return h
+
+
+def bin_feature(counts) -> np.ndarray:
+    """The network input of a bin holding c values: log2(1 + c) / 32."""
+    return np.log2(1.0 + np.asarray(counts, np.float64)) / 32.0
 
 
 def features(degx, degy) -> np.ndarray:
-    return np.concatenate([histogram(degx), histogram(degy)])
+    return np.concatenate([bin_feature(histogram(degx)), bin_feature(histogram(degy))])
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:

@@ -262,8 +262,9 @@ int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
         jp::Partition p;
         double out_est = 0;
         ctx->tm.begin(jp::TM_SELECT);
+        int judged = 0;
         jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
-                              ctx->predictor);
+                              ctx->predictor, &judged);
         ctx->tm.end(jp::TM_SELECT);
         ctx->tm.begin(jp::TM_PARTITION);
         jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
@@ -320,6 +321,7 @@ int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
         s.w = p.w;
         s.light_candidates = lr.candidates;
         s.out_count = count;
+        s.learned_judged = judged;
         s.kernel_launches = jp::g_launches - launches0;
         for (int q = 0; q < 8; ++q) {
             s.light_x[q] = lr.class_x[q];

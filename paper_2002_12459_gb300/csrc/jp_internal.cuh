@@ -136,9 +136,10 @@ void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStre
 
 // Threshold selection (jp_select.cu)
 double out_estimate(double dom_x, double out_join, double N);
+// *judged (JP_LEARNED): 1 the model's thresholds kept, 2 replaced by Algorithm 3's.
 void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
                        int64_t* d2, double* out_est, Arena& ws, cudaStream_t st,
-                       jp_mlp* predictor = nullptr);
+                       jp_mlp* predictor = nullptr, int* judged = nullptr);
 
 // Learned predictor (jp_mlp.cu): the 128 degree features of a built graph and
 // the thresholds a model predicts for them.

@@ -6,8 +6,9 @@
 // model by a network trained on thresholds the GPU method itself found best:
 //
 //  features  two 64-bin log-degree histograms (x degrees; y degrees taken as
-//            max(deg_R(y), deg_S(y)), the partition rule), as fractions of the
-//            values.  bin(d) = min(63, floor(4 log2 d)) is computed exactly
+//            max(deg_R(y), deg_S(y)), the partition rule); a bin holding c
+//            values enters as log2(1 + c) / 32, so the relation's size is
+//            visible.  bin(d) = min(63, floor(4 log2 d)) is computed exactly
 //            with integers: e = floor(log2 d) from the leading-zero count, and
 //            the quarter-octave is found by comparing d * 2^(30 - e) with the
 //            ceilings of 2^(30 + k/4), k = 1, 2, 3.
@@ -217,12 +218,8 @@ void graph_features(const Graph& g, float* host128, Arena& ws, cudaStream_t st) 
     unsigned long long h[128];
     JP_CUDA_TRY(cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, st));
     JP_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int s = 0; s < 2; ++s) {
-        double tot = 0;
-        for (int i = 0; i < 64; ++i) tot += (double)h[s * 64 + i];
-        for (int i = 0; i < 64; ++i)
-            host128[s * 64 + i] = tot > 0 ? (float)((double)h[s * 64 + i] / tot) : 0.0f;
-    }
+    // a bin holding c values enters as log2(1 + c) / 32 (keeps the scale)
+    for (int i = 0; i < 128; ++i) host128[i] = (float)(std::log2(1.0 + (double)h[i]) / 32.0);
 }
 
 // Thresholds predicted for the features (ln outputs exponentiated, floored,

@@ -34,18 +34,47 @@ struct DevHist {
 
 struct Over { long long deg; unsigned long long a, b; };
 
+// lane per x summing its own neighbours' S degrees; the x of a warp with more
+// than 32 neighbours are summed by the whole warp (eight loads in flight per
+// lane), one after another
 __global__ void hist_x_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
                               const int32_t* deg_sy, DevHist* H, Over* xo) {
     const int lane = threadIdx.x & 31;
-    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t a = warp; a < nx; a += nwarps) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < nx;
+         base += stride) {
+        const int64_t a = base + lane;
+        const bool valid = a < nx;
+        int32_t e0 = 0, e1 = 0;
+        if (valid) {
+            e0 = rxoff[a];
+            e1 = rxoff[a + 1];
+        }
+        const bool small = valid && e1 - e0 <= 32;
         unsigned long long c = 0;
-        for (int32_t e = rxoff[a] + lane; e < rxoff[a + 1]; e += 32) c += deg_sy[rycol[e]];
+        if (small)
+            for (int32_t e = e0; e < e1; ++e) c += (unsigned long long)deg_sy[rycol[e]];
+        unsigned big = __ballot_sync(0xffffffffu, valid && !small);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t f0 = __shfl_sync(0xffffffffu, e0, j), f1 = __shfl_sync(0xffffffffu, e1, j);
+            unsigned long long sj = 0;
+            int32_t e = f0 + lane;
+            for (; e + 7 * 32 < f1; e += 8 * 32) {
+                int32_t b[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-        if (lane == 0) {
-            const int32_t d = rxoff[a + 1] - rxoff[a];
+                for (int u = 0; u < 8; ++u) b[u] = rycol[e + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sj += (unsigned long long)deg_sy[b[u]];
+            }
+            for (; e < f1; e += 32) sj += (unsigned long long)deg_sy[rycol[e]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+            if (lane == j) c = sj;
+        }
+        if (valid) {
+            const int32_t d = e1 - e0;
             if (d <= HMAX) {
                 atomicAdd(&H->x_cnt[d], 1ull);
                 atomicAdd(&H->x_cand[d], c);
@@ -156,6 +185,7 @@ struct CostConsts {
     double mm_fixed = 20e-6;
     double eps = 0.05;
     double wcoj_factor = 20.0;
+    double judge = 3.0;        // JP_LEARNED: modelled-cost ratio above which the model is overruled
 };
 
 double out_estimate(double dom_x, double out_join, double N) {
@@ -167,7 +197,8 @@ double out_estimate(double dom_x, double out_join, double N) {
 
 void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
                        int64_t* d2, double* out_est, Arena& ws, cudaStream_t st,
-                       jp_mlp* predictor) {
+                       jp_mlp* predictor, int* judged) {
+    if (judged) *judged = 0;
     const int64_t N = std::max<int64_t>(std::max(g.nr, g.ns), 1);
     *out_est = out_estimate((double)g.nx, g.out_join, (double)g.nr);
     if (mode == JP_FIXED) {
@@ -189,17 +220,21 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
         *d2 = clamp_delta(b, N);
         return;
     }
+    // JP_LEARNED: the model predicts (l1, l2); the cost model below then judges
+    // them against its own choice and keeps them unless they cost more than
+    // K.judge times as much
+    int64_t l1 = 0, l2 = 0;
     if (mode == JP_LEARNED) {
         if (!predictor) throw Error{JP_EINVAL, "JP_LEARNED needs a model (jp_set_predictor)"};
         float f[128];
         graph_features(g, f, ws, st);
-        mlp_predict(predictor, f, N, d1, d2);
-        return;
+        mlp_predict(predictor, f, N, &l1, &l2);
+    } else if (mode != JP_COST_MODEL) {
+        throw Error{JP_EINVAL, "unknown threshold mode"};
     }
-    if (mode != JP_COST_MODEL) throw Error{JP_EINVAL, "unknown threshold mode"};
     // ---- Algorithm 3 on exact degree indexes
     const CostConsts K;
-    if (g.out_join <= K.wcoj_factor * (double)N) {  // plain worst-case optimal join
+    if (mode == JP_COST_MODEL && g.out_join <= K.wcoj_factor * (double)N) {  // plain worst-case optimal join
         *d1 = N;
         *d2 = N;
         return;
@@ -210,7 +245,7 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
     Over* zo = ws.get<Over>(g.nz + 1);
     JP_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(DevHist), st));
     if (g.nx) {
-        hist_x_kernel<<<grid_for(g.nx * 32, 256, 152 * 16), 256, 0, st>>>(g.nx, g.rxoff, g.rycol,
+        hist_x_kernel<<<grid_for(g.nx, 256, 152 * 16), 256, 0, st>>>(g.nx, g.rxoff, g.rycol,
                                                                         g.deg_sy, H, xo);
         JP_CHECK_LAUNCH();
     }
@@ -249,7 +284,8 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
     };
     double a = n, b = std::max(n * a / OUT, 1.0);
     double prev_cost = INFINITY, pa = a, pb = b;
-    for (int it = 0; it < 100000; ++it) {
+    const bool wcoj = g.out_join <= K.wcoj_factor * (double)N;
+    for (int it = 0; it < 100000 && !wcoj; ++it) {
         double c = cost(a, b);
         if (c > prev_cost) break;
         prev_cost = c;
@@ -258,6 +294,16 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
         if (a <= 1.0) break;
         a = std::max(a * (1.0 - K.eps), 1.0);
         b = std::max(n * a / OUT, 1.0);
+    }
+    if (mode == JP_LEARNED) {
+        const double cl = cost((double)l1, (double)l2), ca = cost(pa, pb);
+        if (cl <= K.judge * ca) {
+            *d1 = l1;
+            *d2 = l2;
+            if (judged) *judged = 1;
+            return;
+        }
+        if (judged) *judged = 2;
     }
     *d1 = clamp_delta(pa, N);
     *d2 = clamp_delta(pb, N);

@@ -55,7 +55,7 @@ class jp_stats(ctypes.Structure):
                 ("light_x", ctypes.c_int64 * 8), ("light_cand", ctypes.c_int64 * 8),
                 ("light_deg", ctypes.c_int64 * 8),
                 ("ms_total", ctypes.c_double),
-                ("ms_pass", ctypes.c_double * 16)]
+                ("ms_pass", ctypes.c_double * 16), ("learned_judged", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

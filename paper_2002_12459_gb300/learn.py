@@ -9,15 +9,20 @@ The network is trained with the library's own kernels (jp_mlp_train_step)
 and evaluated on held-out relations: the query time at the predicted
 thresholds is compared with the best grid time ("oracle-best threshold") and
 with the time at the cost-model thresholds (Algorithm 3), which is also the
-fallback when no model is set.
+fallback when no model is set and the judge of every prediction (a
+prediction whose modelled cost exceeds 3x that of Algorithm 3's choice is
+replaced by that choice).
 
-  python -m paper_2002_12459_gb300.learn --train 160 --test 48 --out params.npy
+  python -m paper_2002_12459_gb300.learn --train 200 --test 48 --n-hi 5e6 --max-join 2e9 \
+      --out params.npy --report report.json
+  python -m paper_2002_12459_gb300.learn ... --eval params.npy --report report.json
 """
 from __future__ import annotations
 
 import argparse
 import json
 import math
+import os
 import sys
 import time
 
@@ -179,7 +184,7 @@ def evaluate(ctx, pred, rows, log):
         t_learn, st = query_ms(ctx, r["x"], r["y"], "learned")
         out.append(dict(n=r["spec"]["n"], best=r["best"], t_best=r["t_best"], t_cost=r["t_cost"],
                         t_learned=t_learn, learned_delta=(st["delta1"], st["delta2"]),
-                        cost_delta=r["cost_delta"]))
+                        cost_delta=r["cost_delta"], overruled=st["learned_judged"] == 2))
     ctx.set_predictor(None)
     ratio_l = [o["t_learned"] / o["t_best"] for o in out]
     ratio_c = [o["t_cost"] / o["t_best"] for o in out]
@@ -188,7 +193,8 @@ def evaluate(ctx, pred, rows, log):
                    cost_over_best_geomean=float(np.exp(np.mean(np.log(ratio_c)))),
                    learned_total_ms=float(sum(o["t_learned"] for o in out)),
                    cost_total_ms=float(sum(o["t_cost"] for o in out)),
-                   best_total_ms=float(sum(o["t_best"] for o in out)))
+                   best_total_ms=float(sum(o["t_best"] for o in out)),
+                   overruled_by_cost_model=int(sum(o["overruled"] for o in out)))
     log(f"[learn] held-out: learned/best {summary['learned_over_best_geomean']:.3f}, "
         f"cost-model/best {summary['cost_over_best_geomean']:.3f}")
     return summary, out
@@ -206,6 +212,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None, help="write the trained float32 parameters (.npy)")
     ap.add_argument("--report", default=None, help="write a JSON report")
+    ap.add_argument("--eval", default=None, metavar="PARAMS",
+                    help="no training: evaluate these parameters (.npy) on the held-out relations")
     args = ap.parse_args(argv)
 
     from paper_2002_12459_gb300 import build, jp
@@ -219,12 +227,20 @@ def main(argv=None):
     specs = draw_specs(args.train + args.test, args.seed, args.n_lo, args.n_hi, args.max_join, log)
     ctx = jp.Context(0)
     pred = jp.Predictor(0)
-    X, T, rows = collect(ctx, specs, log)
-    Xtr, Ttr = X[:args.train], T[:args.train]
-    loss = fit(pred, Xtr, Ttr, args.steps, args.lr, args.seed, log)
-    summary, detail = evaluate(ctx, pred, rows[args.train:], log)
-    summary.update(train_relations=args.train, final_train_loss=loss,
-                   seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
+    if args.eval:
+        # the held-out relations are the same ones as when training (same draw)
+        X, T, rows = collect(ctx, specs[args.train:], log)
+        pred.set_params(np.load(args.eval))
+        summary, detail = evaluate(ctx, pred, rows, log)
+        summary.update(train_relations=args.train, evaluated=os.path.basename(args.eval),
+                       seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
+    else:
+        X, T, rows = collect(ctx, specs, log)
+        Xtr, Ttr = X[:args.train], T[:args.train]
+        loss = fit(pred, Xtr, Ttr, args.steps, args.lr, args.seed, log)
+        summary, detail = evaluate(ctx, pred, rows[args.train:], log)
+        summary.update(train_relations=args.train, final_train_loss=loss,
+                       seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
     if args.out:
         np.save(args.out, pred.get_params())
     if args.report:

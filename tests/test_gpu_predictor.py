@@ -73,7 +73,7 @@ def test_feature_bins_at_quarter_octave_edges(env):
     xs = np.concatenate([np.full(d, i) for i, d in enumerate(degs)]).astype(np.int32)
     ys = np.concatenate([np.arange(d) for d in degs]).astype(np.int32)
     f = ctx.features(dev(xs), dev(ys))
-    want = M.histogram(degs)
+    want = M.bin_feature(M.histogram(degs))
     assert np.allclose(f[:64], want, atol=1e-7)
 
 
@@ -140,8 +140,38 @@ def test_learned_mode_uses_the_model(env, oracle_mod):
     st = ctx.stats()
     b = M.bf16_round(params[5])
     want = [int(np.floor(np.exp(np.float64(np.float32(v))))) for v in b]
-    assert (st["delta1"], st["delta2"]) == tuple(want)
+    # the cost model keeps the prediction (1) or overrules it with its own (2)
+    assert st["learned_judged"] in (1, 2)
     wx, wz = oracle_mod.two_path(x, y)
     assert np.array_equal(ox.cpu().numpy(), wx) and np.array_equal(oz.cpu().numpy(), wz)
+    ctx.set_threshold("cost_model")
+    ctx.two_path(dev(x), dev(y))
+    cm = ctx.stats()
+    assert cm["learned_judged"] == 0
+    if st["learned_judged"] == 1:
+        assert (st["delta1"], st["delta2"]) == tuple(want)
+    else:
+        assert (st["delta1"], st["delta2"]) == (cm["delta1"], cm["delta2"])
+    ctx.set_predictor(None)
+    ctx.set_threshold("closed_form")
+
+
+def test_cost_model_overrules_a_costly_prediction(env):
+    # a constant prediction of (1, 1) makes every x of degree > 1 heavy: on this
+    # relation a ~2e4-cube Boolean product, far above the cost model's choice
+    torch, jp, ctx, pred = env
+    params = [np.zeros(s) for s in SHAPES]
+    pred.set_params(flat(params))                      # exp(0) = 1 for both
+    x, y = W.powerlaw_relation(200_000, 40_000, 2.1, 20_000, 1.8, 5)
+    ctx.set_threshold("cost_model")
+    cx, cz = ctx.two_path(dev(x), dev(y))
+    cm = ctx.stats()
+    ctx.set_predictor(pred)
+    ctx.set_threshold("learned")
+    lx, lz = ctx.two_path(dev(x), dev(y))
+    st = ctx.stats()
+    assert st["learned_judged"] == 2
+    assert (st["delta1"], st["delta2"]) == (cm["delta1"], cm["delta2"])
+    assert torch.equal(cx, lx) and torch.equal(cz, lz)
     ctx.set_predictor(None)
     ctx.set_threshold("closed_form")

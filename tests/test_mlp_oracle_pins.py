@@ -25,12 +25,22 @@ def test_log_degree_bins_match_the_definition():
             assert 2 ** k <= d ** 4 < 2 ** (k + 1)
 
 
-def test_histogram_is_a_distribution():
+def test_histogram_counts_and_bin_feature_scale():
     rng = np.random.default_rng(0)
     d = rng.integers(1, 10 ** 6, 1000)
     h = M.histogram(d)
-    assert h.shape == (64,) and abs(h.sum() - 1.0) < 1e-12 and (h >= 0).all()
+    assert h.shape == (64,) and h.sum() == 1000 and (h >= 0).all()
     assert M.histogram([0, 0]).sum() == 0.0
+    # log2(1 + c) / 32: empty bins give 0, one value 1/32, 2^32 - 1 values 1
+    assert M.bin_feature([0, 1, 3, 2 ** 32 - 1]).tolist() == [0.0, 1 / 32, 2 / 32, 1.0]
+    # doubling a bin's population (c -> 2c + 1) raises its feature by exactly 1/32
+    c = rng.integers(0, 10 ** 9, 100).astype(np.float64)
+    assert np.allclose(M.bin_feature(2 * c + 1) - M.bin_feature(c), 1 / 32, atol=1e-15)
+    # a relation with every degree count doubled sees every populated bin move up
+    f1 = M.features(d, d)
+    f2 = M.features(np.repeat(d, 2), np.repeat(d, 2))
+    pop = M.histogram(d) > 0
+    assert (f2[:64][pop] > f1[:64][pop]).all() and (f2[:64][~pop] == 0).all()
 
 
 def test_bf16_rounding():
