@@ -689,6 +689,7 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
     __shared__ uint32_t s_pre[BM_THREADS];     // prefix of the neighbour list lengths
     __shared__ int32_t s_start[BM_THREADS];    // list start (negative: in slcol)
     __shared__ uint32_t s_item[2];             // work items of this row and the next
+    __shared__ uint32_t s_total;               // candidates of a flattened row
     const uint32_t nh = qc->q[Q_HUB], nq = nh + qc->q[Q_BITMAP];
     const int64_t win_bits = (int64_t)win_words * 32;
     for (int32_t i = threadIdx.x; i < win_words + win_words / 32; i += blockDim.x) smem_bm[i] = 0;
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                     }
                     const int32_t excl = incl - L;
                     const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                    constexpr int UH = 4;
+                    constexpr int UH = 8;
                     for (int32_t f0 = 0; f0 < total; f0 += 32 * UH) {
                         int32_t zz[UH];
 #pragma unroll
@@ -769,33 +770,56 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                     }
                 }
             }
-            // other rows: flattened over the whole block: neighbours are taken
-            // BM_THREADS at a time, their list lengths prefix-summed, and
-            // thread t handles flat candidates t, t + BM_THREADS, ... (adjacent
-            // threads read adjacent list entries)
-            for (int32_t c0 = 0; deg < BM_WARP_PER_LIST && c0 < deg; c0 += BM_THREADS) {
-                const int32_t i = c0 + threadIdx.x;
-                int32_t start = 0, L = 0;
-                if (i < deg) {
-                    const int32_t b = A.rycol[e0 + i];
-                    const int32_t j = heavy ? A.hy[b] : -1;
-                    if (j >= 0) {          // light z of a heavy y: negative = slcol offset
-                        start = -A.sloff[j] - 1;
-                        L = A.sloff[j + 1] - A.sloff[j];
-                    } else {
-                        start = A.syoff[b];
-                        L = A.syoff[b + 1] - start;
+            // other rows (fewer than BM_WARP_PER_LIST = 128 neighbour lists):
+            // warp 0 reads the lists' bounds (four per lane) and prefix-sums
+            // their lengths; then thread t handles flat candidates t,
+            // t + BM_THREADS, ... (adjacent threads read adjacent list entries)
+            if (deg < BM_WARP_PER_LIST) {
+                if (threadIdx.x < 32) {
+                    const int lane = threadIdx.x;
+                    int32_t st4[4], L4[4], sum = 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = 4 * lane + k;
+                        st4[k] = 0;
+                        L4[k] = 0;
+                        if (i < deg) {
+                            const int32_t b = A.rycol[e0 + i];
+                            const int32_t j = heavy ? A.hy[b] : -1;
+                            if (j >= 0) {      // light z of a heavy y: negative = slcol offset
+                                st4[k] = -A.sloff[j] - 1;
+                                L4[k] = A.sloff[j + 1] - A.sloff[j];
+                            } else {
+                                st4[k] = A.syoff[b];
+                                L4[k] = A.syoff[b + 1] - st4[k];
+                            }
+                        }
+                        sum += L4[k];
                     }
+                    int32_t inc = sum;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    int32_t run = inc - sum;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = 4 * lane + k;
+                        if (i < deg) {
+                            s_pre[i] = (uint32_t)run;
+                            s_start[i] = st4[k];
+                        }
+                        run += L4[k];
+                    }
+                    if (lane == 31) s_total = (uint32_t)inc;
                 }
-                uint32_t total;
-                const uint32_t ex = block_exclusive<uint32_t>((uint32_t)L, sw, &total);
-                s_pre[threadIdx.x] = ex;
-                s_start[threadIdx.x] = start;
                 __syncthreads();
-                const int32_t nn = min(BM_THREADS, deg - c0);
-                constexpr int U = 4;    // candidates loaded before any is marked
+                const uint32_t total = s_total;
+                const int32_t nn = deg;
+                constexpr int U = 8;    // candidates loaded before any is marked
                 for (uint32_t f0 = threadIdx.x; f0 < total; f0 += U * BM_THREADS) {
-                    int64_t zz[U];
+                    int32_t zz[U];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const uint32_t f = f0 + (uint32_t)u * BM_THREADS;
@@ -815,7 +839,8 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                     for (int u = 0; u < U; ++u)
                         if (zz[u] >= z0 && zz[u] < zend) mark(bm, summ, (int32_t)(zz[u] - z0));
                 }
-                __syncthreads();
+                // s_pre and s_start are next written after the barrier that ends
+                // the marking phase below
             }
             // heavy product row: bit l of G[h] means (a, hz_inv[l]) is an output
             if (heavy && A.G) {
@@ -851,8 +876,29 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                     mine += __popc(bm[s * 32 + j]);
                 }
             }
-            uint32_t tot;
-            const uint32_t ex = block_exclusive<uint32_t>(mine, sw, &tot);
+            // exclusive prefix of the threads' counts: warp scans, then the warp
+            // totals through shared memory (one barrier)
+            uint32_t ex, tot;
+            {
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                uint32_t inc = mine;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                if (lane == 31) sw[warp] = inc;
+                __syncthreads();
+                const uint32_t v = sw[lane];
+                uint32_t before = lane < warp ? v : 0u;
+                tot = v;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    before += __shfl_xor_sync(0xffffffffu, before, o);
+                    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                }
+                ex = before + inc - mine;
+            }
             unsigned long long p = base + running + ex;
             const unsigned long long lim = base + ub;
             for (int32_t s = lo; s < hi; ++s) {
