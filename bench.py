@@ -295,6 +295,28 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
 
+    # end to end through the C-ABI with host buffers, right after the timed
+    # steps (same workspace and allocator state as the steps it is compared with)
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        hrx = torch.from_numpy(rx).pin_memory()
+        hry = torch.from_numpy(ry).pin_memory()
+        cols = [torch.empty(out + 1, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        times, split = [], {}
+        for i in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gx, gz = ctx.two_path_host(hrx, hry, cols, timings=split if i > 0 else None)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+            del gx, gz
+        k = len(times)
+        e2e = {"value": out / (sum(times) / k), "unit": UNIT,
+               "h2d_bytes_per_step": int(8 * len(rx)), "d2h_bytes_per_step": int(8 * out),
+               "ms_per_step": 1e3 * sum(times) / k,
+               "ms_split": {n: round(1e3 * v / k, 2) for n, v in split.items()}}
+
     # the same query at the learned thresholds (the shipped predictor), timed
     # the same way, against the cost-model thresholds above
     learned = None
@@ -321,25 +343,6 @@ def run_ours(args, rank, world, local_rank):
         parity = {"rows_checked": len(sample), "bit_exact": ok}
         del hx, hz
     del ox, oz
-
-    # end to end through the C-ABI with host buffers
-    e2e = None
-    if rank == 0 and not args.no_e2e:
-        hrx = torch.from_numpy(rx).pin_memory()
-        hry = torch.from_numpy(ry).pin_memory()
-        cols = [torch.empty(out + 1, dtype=torch.int32, pin_memory=True) for _ in range(2)]
-        times = []
-        for i in range(1 + args.e2e_steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            gx, gz = ctx.two_path_host(hrx, hry, cols)
-            torch.cuda.synchronize()
-            if i > 0:
-                times.append(time.perf_counter() - t0)
-            del gx, gz
-        e2e = {"value": out / (sum(times) / len(times)), "unit": UNIT,
-               "h2d_bytes_per_step": int(8 * len(rx)), "d2h_bytes_per_step": int(8 * out),
-               "ms_per_step": 1e3 * sum(times) / len(times)}
 
     base = None
     if rank == 0 and not args.no_cpu:

@@ -139,6 +139,21 @@ int jp_set_stream(jp_ctx* ctx, void* stream);
  * distinct (x, z) pairs, k = 2.  R->n + S->n must stay below 2^31. */
 int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out);
 
+/* Batch of two-path self-joins Q_q(x,z) = R_q(x,y), R_q(z,y), q = 0..nq-1, evaluated in
+ * one pass of the pipeline (each pass one launch over all queries).  Every value is tagged
+ * with its query ((query, value) pairs are dictionary-encoded), so the batch is the single
+ * self-join of the disjoint union: no pair mixes two queries, and the thresholds are chosen
+ * for the union by the context's mode.
+ *   all      the queries' tuples one after another (device or host columns, as jp_two_path);
+ *   qoff     host, nq + 1 entries: query q holds tuples [qoff[q], qoff[q+1]); qoff[0] = 0,
+ *            qoff[nq] = all->n, non-decreasing (empty queries are allowed);
+ *   out      one result (k = 2) holding the queries' sorted distinct pairs, query after query;
+ *   out_off  host, nq + 1 entries, receives where each query's pairs start (out_off[nq] =
+ *            out->count).
+ * Errors as jp_two_path; JP_EINVAL for bad offsets. */
+int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t* qoff,
+                      jp_result* out, int64_t* out_off);
+
 /* Star query Q*_k (Section 2.1, Section 3.2) over rels[0..k-1], 2 <= k <= 8;
  * on success *out holds the sorted distinct k-tuples. */
 int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out);

@@ -149,6 +149,150 @@ void status_check(jp_ctx* ctx) {
 
 }  // namespace
 
+namespace {
+
+struct BatchArgs {
+    int32_t nq;
+    const int64_t* qoff;     // host, nq + 1
+    int64_t* out_off;        // host, nq + 1
+};
+
+// The two-path pipeline.  With a batch, R holds the queries' tuples one after
+// another (batch->qoff) and is a self-join per query; its values are first
+// encoded to (query, value) ids, and the output maps them back.
+int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
+                 const BatchArgs* batch) {
+    if (!ctx) return JP_EINVAL;
+    if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->k = 2;
+    int rc = check_rel(ctx, R, "R");
+    if (rc) return rc;
+    if (S && (rc = check_rel(ctx, S, "S"))) return rc;
+    if (S && R->n + S->n >= ((int64_t)1 << 31)) return fail(ctx, JP_EUNSUPPORTED, "R and S together hold 2^31 or more tuples");
+    const auto t_start = std::chrono::steady_clock::now();
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = ctx->stream;
+        ctx->ws.begin();
+        const int64_t launches0 = jp::g_launches;
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
+        for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
+        ctx->tm.st = st;
+        jp::g_timer = &ctx->tm;
+        ctx->tm.begin(jp::TM_TOTAL);
+        jp_rel Rd = to_device(ctx, R);
+        jp_rel Sd;
+        if (S) Sd = to_device(ctx, S);
+        const bool self = (S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n);
+        jp::BatchIds bid;
+        if (batch) {
+            jp::batch_encode(Rd.x, Rd.y, Rd.n, batch->nq, batch->qoff, bid, ctx->ws, st,
+                             ctx->hist_host, ctx->d_status);
+            Rd.x = bid.xg;
+            Rd.y = bid.yg;
+        }
+
+        jp::Graph g;
+        ctx->tm.begin(jp::TM_BUILD);
+        jp::build_graph(&Rd, self ? nullptr : &Sd, g, ctx->ws, st, ctx->d_status, ctx->hist_host,
+                        ctx->host_scalars);
+        ctx->tm.end(jp::TM_BUILD);
+
+        jp::Partition p;
+        double out_est = 0;
+        ctx->tm.begin(jp::TM_SELECT);
+        int judged = 0;
+        jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
+                              ctx->predictor, &judged);
+        ctx->tm.end(jp::TM_SELECT);
+        ctx->tm.begin(jp::TM_PARTITION);
+        jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
+        ctx->tm.end(jp::TM_PARTITION);
+
+        jp::Heavy h;
+        ctx->tm.begin(jp::TM_PACK);
+        jp::heavy_pack(g, p, h, ctx->ws, st);
+        ctx->tm.end(jp::TM_PACK);
+        jp::heavy_gemm(h, p, ctx->d_status, st, nullptr);
+
+        jp::LightResult lr;
+        jp::light_and_union(g, p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars);
+
+        int64_t* out_off = ctx->ws.get<int64_t>(g.nx + 1);
+        ctx->tm.begin(jp::TM_COUNT);
+        const int64_t count = jp::output_count(g, lr, out_off, ctx->ws, st, ctx->host_scalars);
+        ctx->tm.end(jp::TM_COUNT);
+        status_check(ctx);
+        if (count > 0) {
+            block_bytes = (size_t)count * 2 * sizeof(int32_t) + 512;
+            block = ctx->ws.raw_alloc(block_bytes);
+            if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
+            int32_t* ox = reinterpret_cast<int32_t*>(block);
+            int32_t* oz = reinterpret_cast<int32_t*>(
+                reinterpret_cast<char*>(block) + (((size_t)count * sizeof(int32_t) + 255) & ~(size_t)255));
+            ctx->tm.begin(jp::TM_PLACE);
+            if (batch)
+                jp::output_write_mapped(g, lr, out_off, count, bid.xorig, ox, oz, st);
+            else
+                jp::output_write(g, lr, out_off, count, ox, oz, st);
+            ctx->tm.end(jp::TM_PLACE);
+            out->col[0] = ox;
+            out->col[1] = oz;
+        }
+        if (batch) jp::batch_offsets(out_off, g.nx, count, bid, batch->nq, batch->out_off, ctx->ws, st);
+        ctx->tm.end(jp::TM_TOTAL);
+        status_check(ctx);
+        jp::g_timer = nullptr;
+        out->count = count;
+        out->_block = block;
+        out->_bytes = block_bytes;
+
+        jp_stats& s = ctx->stats;
+        std::memset(&s, 0, sizeof(s));
+        s.n_r = g.nr;
+        s.n_s = g.ns;
+        s.dom_x = g.nx;
+        s.dom_y = g.ny;
+        s.dom_z = g.nz;
+        s.out_join = g.out_join;
+        s.out_estimate = out_est;
+        s.delta1 = p.d1;
+        s.delta2 = p.d2;
+        s.threshold_mode = ctx->mode;
+        s.u = p.u;
+        s.v = p.v;
+        s.w = p.w;
+        s.light_candidates = lr.candidates;
+        s.out_count = count;
+        s.learned_judged = judged;
+        s.kernel_launches = jp::g_launches - launches0;
+        for (int q = 0; q < 8; ++q) {
+            s.light_x[q] = lr.class_x[q];
+            s.light_cand[q] = lr.class_cand[q];
+            s.light_deg[q] = lr.class_deg[q];
+        }
+        for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
+        s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        ctx->have_stats = true;
+        ctx->err.clear();
+        return JP_OK;
+    } catch (const jp::Error& e) {
+        jp::g_timer = nullptr;
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, e.code, e.msg);
+    } catch (const std::bad_alloc&) {
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, JP_ENOMEM, "host allocation failed");
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 int jp_create(jp_ctx** out, int device, void* stream, jp_alloc_fn alloc, jp_free_fn release,
@@ -227,122 +371,23 @@ int jp_set_stream(jp_ctx* ctx, void* stream) {
 }
 
 int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
+    return run_two_path(ctx, R, S, out, nullptr);
+}
+
+int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t* qoff,
+                      jp_result* out, int64_t* out_off) {
     if (!ctx) return JP_EINVAL;
     if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
     std::memset(out, 0, sizeof(*out));
     out->k = 2;
-    int rc = check_rel(ctx, R, "R");
-    if (rc) return rc;
-    if (S && (rc = check_rel(ctx, S, "S"))) return rc;
-    if (S && R->n + S->n >= ((int64_t)1 << 31)) return fail(ctx, JP_EUNSUPPORTED, "R and S together hold 2^31 or more tuples");
-    const auto t_start = std::chrono::steady_clock::now();
-    void* block = nullptr;
-    size_t block_bytes = 0;
-    try {
-        JP_CUDA_TRY(cudaSetDevice(ctx->device));
-        cudaStream_t st = ctx->stream;
-        ctx->ws.begin();
-        const int64_t launches0 = jp::g_launches;
-        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
-        for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
-        ctx->tm.st = st;
-        jp::g_timer = &ctx->tm;
-        ctx->tm.begin(jp::TM_TOTAL);
-        jp_rel Rd = to_device(ctx, R);
-        jp_rel Sd;
-        if (S) Sd = to_device(ctx, S);
-        const bool self = (S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n);
-
-        jp::Graph g;
-        ctx->tm.begin(jp::TM_BUILD);
-        jp::build_graph(&Rd, self ? nullptr : &Sd, g, ctx->ws, st, ctx->d_status, ctx->hist_host,
-                        ctx->host_scalars);
-        ctx->tm.end(jp::TM_BUILD);
-
-        jp::Partition p;
-        double out_est = 0;
-        ctx->tm.begin(jp::TM_SELECT);
-        int judged = 0;
-        jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
-                              ctx->predictor, &judged);
-        ctx->tm.end(jp::TM_SELECT);
-        ctx->tm.begin(jp::TM_PARTITION);
-        jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
-        ctx->tm.end(jp::TM_PARTITION);
-
-        jp::Heavy h;
-        ctx->tm.begin(jp::TM_PACK);
-        jp::heavy_pack(g, p, h, ctx->ws, st);
-        ctx->tm.end(jp::TM_PACK);
-        jp::heavy_gemm(h, p, ctx->d_status, st, nullptr);
-
-        jp::LightResult lr;
-        jp::light_and_union(g, p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars);
-
-        int64_t* out_off = ctx->ws.get<int64_t>(g.nx + 1);
-        ctx->tm.begin(jp::TM_COUNT);
-        const int64_t count = jp::output_count(g, lr, out_off, ctx->ws, st, ctx->host_scalars);
-        ctx->tm.end(jp::TM_COUNT);
-        status_check(ctx);
-        if (count > 0) {
-            block_bytes = (size_t)count * 2 * sizeof(int32_t) + 512;
-            block = ctx->ws.raw_alloc(block_bytes);
-            if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
-            int32_t* ox = reinterpret_cast<int32_t*>(block);
-            int32_t* oz = reinterpret_cast<int32_t*>(
-                reinterpret_cast<char*>(block) + (((size_t)count * sizeof(int32_t) + 255) & ~(size_t)255));
-            ctx->tm.begin(jp::TM_PLACE);
-            jp::output_write(g, lr, out_off, count, ox, oz, st);
-            ctx->tm.end(jp::TM_PLACE);
-            out->col[0] = ox;
-            out->col[1] = oz;
-        }
-        ctx->tm.end(jp::TM_TOTAL);
-        status_check(ctx);
-        jp::g_timer = nullptr;
-        out->count = count;
-        out->_block = block;
-        out->_bytes = block_bytes;
-
-        jp_stats& s = ctx->stats;
-        std::memset(&s, 0, sizeof(s));
-        s.n_r = g.nr;
-        s.n_s = g.ns;
-        s.dom_x = g.nx;
-        s.dom_y = g.ny;
-        s.dom_z = g.nz;
-        s.out_join = g.out_join;
-        s.out_estimate = out_est;
-        s.delta1 = p.d1;
-        s.delta2 = p.d2;
-        s.threshold_mode = ctx->mode;
-        s.u = p.u;
-        s.v = p.v;
-        s.w = p.w;
-        s.light_candidates = lr.candidates;
-        s.out_count = count;
-        s.learned_judged = judged;
-        s.kernel_launches = jp::g_launches - launches0;
-        for (int q = 0; q < 8; ++q) {
-            s.light_x[q] = lr.class_x[q];
-            s.light_cand[q] = lr.class_cand[q];
-            s.light_deg[q] = lr.class_deg[q];
-        }
-        for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
-        s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-        ctx->have_stats = true;
-        ctx->err.clear();
-        return JP_OK;
-    } catch (const jp::Error& e) {
-        jp::g_timer = nullptr;
-        if (block) ctx->ws.raw_free(block, block_bytes);
-        std::memset(out, 0, sizeof(*out));
-        return fail(ctx, e.code, e.msg);
-    } catch (const std::bad_alloc&) {
-        if (block) ctx->ws.raw_free(block, block_bytes);
-        std::memset(out, 0, sizeof(*out));
-        return fail(ctx, JP_ENOMEM, "host allocation failed");
-    }
+    if (!all || !qoff || !out_off) return fail(ctx, JP_EINVAL, "NULL argument");
+    if (nq < 1) return fail(ctx, JP_EINVAL, "a batch needs at least one query");
+    if (qoff[0] != 0 || qoff[nq] != all->n)
+        return fail(ctx, JP_EINVAL, "query offsets must start at 0 and end at the tuple count");
+    for (int32_t q = 0; q < nq; ++q)
+        if (qoff[q + 1] < qoff[q]) return fail(ctx, JP_EINVAL, "query offsets must not decrease");
+    const BatchArgs b{nq, qoff, out_off};
+    return run_two_path(ctx, all, nullptr, out, &b);
 }
 
 int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {

@@ -63,7 +63,8 @@ __global__ void tile_start_kernel(const int64_t* __restrict__ out_off, int64_t n
 // writes outputs o0 + t + k*OUT_THREADS, so each store instruction of a warp
 // covers 32 consecutive outputs.
 // X2: a second row column (the star's x2) is written next to the first.
-template <bool X2>
+// VMAP: x and z values are ids into vmap, which gives the written values.
+template <bool X2, bool VMAP>
 __global__ void __launch_bounds__(OUT_THREADS)
     place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int32_t* __restrict__ tile_x,
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(OUT_THREADS)
                              const int32_t* __restrict__ xval, const int32_t* __restrict__ xval2,
                              const int32_t* __restrict__ zval, int64_t count,
                              int32_t* __restrict__ out_x, int32_t* __restrict__ out_x2,
-                             int32_t* __restrict__ out_z) {
+                             int32_t* __restrict__ out_z, const int32_t* __restrict__ vmap) {
     __shared__ int64_t s_off[OUT_SX + 1];
     __shared__ int64_t s_toff[OUT_SX];
     __shared__ int32_t s_xv[OUT_SX];
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(OUT_THREADS)
         for (int64_t i = threadIdx.x; i < nxs; i += OUT_THREADS) {
             s_off[i] = out_off[xlo + i];
             s_toff[i] = tmp_off[xlo + i];
-            s_xv[i] = xval[xlo + i];
+            s_xv[i] = VMAP ? vmap[xval[xlo + i]] : xval[xlo + i];
             if (X2) s_xv2[i] = xval2[xlo + i];
         }
         if (threadIdx.x == 0) s_off[nxs] = (xhi < nx) ? out_off[xhi] : count;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(OUT_THREADS)
             } else {
                 const int64_t x = find_x(out_off, xlo, xhi, o);
                 zv[k] = list_at(tmp, szval, tmp_off[x], o - out_off[x], &is_id);
-                xv[k] = xval[x];
+                xv[k] = VMAP ? vmap[xval[x]] : xval[x];
                 if (X2) xv2[k] = xval2[x];
             }
         }
@@ -124,6 +125,11 @@ __global__ void __launch_bounds__(OUT_THREADS)
 #pragma unroll
     for (int k = 0; k < OUT_VT; ++k)
         if (ids >> k & 1u) zv[k] = zval[zv[k]];
+    if (VMAP) {
+#pragma unroll
+        for (int k = 0; k < OUT_VT; ++k)
+            if (o0 + threadIdx.x + (int64_t)k * OUT_THREADS <= o_last) zv[k] = vmap[zv[k]];
+    }
 #pragma unroll
     for (int k = 0; k < OUT_VT; ++k) {
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
@@ -174,13 +180,25 @@ void output_write_rows(const Graph& g, const LightResult& lr, const int64_t* out
     const int64_t per_block = (int64_t)OUT_THREADS * OUT_VT;
     const int64_t blocks = (count + per_block - 1) / per_block;
     if (rowval2 && out_row2)
-        place_kernel<true><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
+        place_kernel<true, false><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
             out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp, lr.szval, rowval, rowval2, g.zval, count,
-            out_row, out_row2, out_z);
+            out_row, out_row2, out_z, nullptr);
     else
-        place_kernel<false><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
+        place_kernel<false, false><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
             out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp, lr.szval, rowval, nullptr, g.zval, count,
-            out_row, nullptr, out_z);
+            out_row, nullptr, out_z, nullptr);
+    JP_CHECK_LAUNCH();
+}
+
+void output_write_mapped(const Graph& g, const LightResult& lr, const int64_t* out_off,
+                         int64_t count, const int32_t* vmap, int32_t* out_x, int32_t* out_z,
+                         cudaStream_t st) {
+    if (count <= 0) return;
+    const int64_t per_block = (int64_t)OUT_THREADS * OUT_VT;
+    const int64_t blocks = (count + per_block - 1) / per_block;
+    place_kernel<false, true><<<(unsigned)blocks, OUT_THREADS, 0, st>>>(
+        out_off, g.nx, lr.tile_x, lr.tmp_off, lr.tmp, lr.szval, g.xval, nullptr, g.zval, count,
+        out_x, nullptr, out_z, vmap);
     JP_CHECK_LAUNCH();
 }
 

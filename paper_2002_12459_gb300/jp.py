@@ -86,6 +86,11 @@ def load(path: str = LIB_PATH):
             lib.jp_two_path.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
                                         ctypes.POINTER(jp_result)]
             lib.jp_two_path.restype = i32
+            lib.jp_two_path_batch.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(jp_result),
+                                              ctypes.POINTER(ctypes.c_int64)]
+            lib.jp_two_path_batch.restype = i32
             lib.jp_star.argtypes = [vp, i32, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
             lib.jp_star.restype = i32
             lib.jp_get_stats.argtypes = [vp, ctypes.POINTER(jp_stats)]
@@ -193,6 +198,28 @@ class Context:
         self._check(rc)
         return self._take(res)
 
+    def two_path_batch(self, x, y, qoff):
+        """Batch of self-joins: query q is tuples [qoff[q], qoff[q+1]) of (x, y).
+
+        Returns (ox, oz, out_off): the queries' sorted distinct pairs one after
+        another and, as a numpy int64 array of nq + 1 entries, where each
+        query's pairs start.
+        """
+        import numpy as np
+        qoff = np.ascontiguousarray(qoff, dtype=np.int64)
+        nq = len(qoff) - 1
+        out_off = np.zeros(nq + 1, np.int64)
+        R = _rel_of(x, y)
+        res = jp_result()
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        with self._torch.cuda.stream(self.stream):
+            rc = self.lib.jp_two_path_batch(self.h, ctypes.byref(R), nq,
+                                            qoff.ctypes.data_as(i64p), ctypes.byref(res),
+                                            out_off.ctypes.data_as(i64p))
+        self._check(rc)
+        ox, oz = self._take(res)
+        return ox, oz, out_off
+
     def star(self, rels):
         """Sorted distinct k-tuples of Q*_k over ``rels = [(x1, y1), ...]``."""
         k = len(rels)
@@ -203,25 +230,37 @@ class Context:
         self._check(rc)
         return self._take(res)
 
-    def two_path_host(self, rx, ry, out_cols=None):
+    def two_path_host(self, rx, ry, out_cols=None, timings=None):
         """End-to-end call with HOST input columns (pinned torch CPU tensors).
 
         The library copies the inputs to the device; the result is copied
-        back into pinned host tensors with jp_result_to_host.
+        back into pinned host tensors with jp_result_to_host.  If ``timings``
+        is a dict it receives the wall seconds of the query call ("query"),
+        the copy to host ("to_host") and the release ("free").
         """
+        import time
         torch = self._torch
         R = _rel_of(rx, ry)
         res = jp_result()
+        t0 = time.perf_counter()
         with torch.cuda.stream(self.stream):
             self._check(self.lib.jp_two_path(self.h, ctypes.byref(R), None, ctypes.byref(res)))
+        t1 = time.perf_counter()
         n = res.count
         if out_cols is None or out_cols[0].numel() < n:
             out_cols = [torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True) for _ in range(2)]
         ptrs = (ctypes.c_void_p * 2)(out_cols[0].data_ptr(), out_cols[1].data_ptr())
+        t2 = t1
         try:
             self._check(self.lib.jp_result_to_host(self.h, ctypes.byref(res), ptrs))
+            t2 = time.perf_counter()
         finally:
             self.lib.jp_result_free(self.h, ctypes.byref(res))
+        if timings is not None:
+            t3 = time.perf_counter()
+            timings["query"] = timings.get("query", 0.0) + (t1 - t0)
+            timings["to_host"] = timings.get("to_host", 0.0) + (t2 - t1)
+            timings["free"] = timings.get("free", 0.0) + (t3 - t2)
         return out_cols[0][:n], out_cols[1][:n]
 
     def stats(self) -> dict:

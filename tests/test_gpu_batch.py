@@ -1,0 +1,125 @@
+"""Batches of two-path self-joins in one pipeline pass (jp_two_path_batch).
+
+Every query of a batch must come out exactly as the oracle answers it alone:
+the queries share values on purpose (a small common domain), so a pair
+mixing two queries, or a lost tagging, shows up as a wrong slice.  Batches
+mix empty, single-tuple and skewed relations, and run at thresholds that
+make everything heavy (one product over the union's heavy block), everything
+light, and the cost model's choice.
+"""
+import numpy as np
+import pytest
+
+from paper_2002_12459_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2002_12459_gb300 import build, jp
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for the -m gpu tests")
+    c = jp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def mixed_batch(seed, nq=40):
+    rng = np.random.default_rng(seed)
+    rels = []
+    for q in range(nq):
+        kind = q % 8
+        if kind == 0:
+            n = 0
+        elif kind == 1:
+            n = 1
+        else:
+            n = int(rng.integers(2, 3000))
+        x = rng.integers(-60, 200, n).astype(np.int32)           # a domain shared by all queries
+        y = (rng.zipf(1.6, n) % 90 - 20).astype(np.int32)
+        if kind == 7 and n:                                       # duplicates and a hub
+            x[: n // 2] = 5
+        rels.append((x, y))
+    return rels
+
+
+def concat(rels):
+    qoff = np.zeros(len(rels) + 1, np.int64)
+    qoff[1:] = np.cumsum([len(x) for x, _ in rels])
+    x = np.concatenate([x for x, _ in rels]).astype(np.int32)
+    y = np.concatenate([y for _, y in rels]).astype(np.int32)
+    return x, y, qoff
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("mode,d", [("fixed", 1), ("fixed", 10 ** 6), ("fixed", 4), ("cost_model", 1)])
+def test_batch_equals_each_query_alone(ctx, oracle_mod, seed, mode, d):
+    rels = mixed_batch(seed)
+    x, y, qoff = concat(rels)
+    ctx.set_threshold(mode, d, d)
+    ox, oz, off = ctx.two_path_batch(dev(x), dev(y), qoff)
+    st = ctx.stats()
+    ox, oz = ox.cpu().numpy(), oz.cpu().numpy()
+    assert off[0] == 0 and off[-1] == len(ox) == st["out_count"]
+    if mode == "fixed" and d == 1:
+        assert st["u"] > 0                   # the union's heavy product ran
+    for q, (rx, ry) in enumerate(rels):
+        wx, wz = oracle_mod.two_path(rx, ry)
+        s, e = off[q], off[q + 1]
+        assert np.array_equal(ox[s:e], wx) and np.array_equal(oz[s:e], wz), q
+
+
+def test_batch_from_host_columns_and_single_query(ctx, oracle_mod):
+    import torch
+    rels = mixed_batch(11, nq=9)
+    x, y, qoff = concat(rels)
+    ctx.set_threshold("cost_model")
+    hx = torch.from_numpy(x).pin_memory()
+    hy = torch.from_numpy(y).pin_memory()
+    ox, oz, off = ctx.two_path_batch(hx, hy, qoff)
+    ox, oz = ox.cpu().numpy(), oz.cpu().numpy()
+    for q, (rx, ry) in enumerate(rels):
+        wx, wz = oracle_mod.two_path(rx, ry)
+        assert np.array_equal(ox[off[q]:off[q + 1]], wx) and np.array_equal(oz[off[q]:off[q + 1]], wz)
+    # a batch of one query is that query
+    rx, ry = rels[3]
+    bx, bz, off1 = ctx.two_path_batch(dev(rx), dev(ry), np.array([0, len(rx)]))
+    gx, gz = ctx.two_path(dev(rx), dev(ry))
+    assert off1.tolist() == [0, gx.numel()]
+    assert torch.equal(bx, gx) and torch.equal(bz, gz)
+
+
+def test_power_law_batch_against_single_queries(ctx):
+    # uneven sizes, 1e3 to 2e5 tuples, with heavy hubs: every slice equals the
+    # query run alone at the same thresholds
+    import torch
+    rng = np.random.default_rng(3)
+    rels = []
+    for q in range(12):
+        n = int(np.exp(rng.uniform(np.log(1e3), np.log(2e5))))
+        rels.append(W.powerlaw_relation(n, max(n // 5, 1), float(rng.uniform(1.3, 2.2)),
+                                        max(n // 10, 1), float(rng.uniform(1.3, 2.2)), 100 + q))
+    x, y, qoff = concat(rels)
+    for d1, d2 in [(16, 8), (200, 40)]:
+        ctx.set_threshold("fixed", d1, d2)
+        ox, oz, off = ctx.two_path_batch(dev(x), dev(y), qoff)
+        for q, (rx, ry) in enumerate(rels):
+            gx, gz = ctx.two_path(dev(rx), dev(ry))
+            assert torch.equal(ox[off[q]:off[q + 1]], gx) and torch.equal(oz[off[q]:off[q + 1]], gz), q
+
+
+def test_bad_offsets_are_rejected(ctx):
+    from paper_2002_12459_gb300 import jp
+    x = dev(np.arange(10))
+    with pytest.raises(jp.JPError, match="EINVAL"):
+        ctx.two_path_batch(x, x, np.array([0, 5, 3, 10]))
+    with pytest.raises(jp.JPError, match="EINVAL"):
+        ctx.two_path_batch(x, x, np.array([0, 9]))
