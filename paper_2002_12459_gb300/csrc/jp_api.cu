@@ -219,7 +219,8 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         jp::heavy_gemm(h, p, ctx->d_status, st, nullptr);
 
         jp::LightResult lr;
-        jp::light_and_union(g, p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars);
+        jp::light_and_union(g, p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars,
+                            batch ? bid.xq_begin : nullptr, batch ? batch->nq : 0);
 
         int64_t* out_off = ctx->ws.get<int64_t>(g.nx + 1);
         ctx->tm.begin(jp::TM_COUNT);

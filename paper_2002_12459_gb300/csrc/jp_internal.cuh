@@ -195,8 +195,11 @@ struct LightResult {
     int64_t class_deg[8] = {};    // neighbour entries
     int32_t* tile_x = nullptr;             // x holding the first output of each output tile
 };
+// qbeg/nq: for batches, the first x id of every query (nq + 1 entries), which
+// bounds the z range of a row; null otherwise.
 void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightResult& lr,
-                     Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars);
+                     Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars,
+                     const int32_t* qbeg = nullptr, int32_t nq = 0);
 
 // Output (jp_output.cu)
 int64_t output_count(const Graph& g, LightResult& lr, int64_t* out_off, Arena& ws,

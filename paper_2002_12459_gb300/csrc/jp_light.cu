@@ -58,7 +58,6 @@ struct Counters {
     unsigned long long q_cand[NQ];    // candidates per class
     unsigned long long q_deg[NQ];     // neighbour-list entries read per class
     uint32_t bm_next;                 // bitmap kernel work counter (hubs, then the rest)
-    int32_t vmin, vmax;               // smallest and largest z value
 };
 
 __device__ __forceinline__ uint32_t next_pow2(uint32_t v) {
@@ -269,8 +268,8 @@ struct LightArgs {
     const int32_t* syoff;
     const int32_t* szcol;
     const int32_t* szval;      // zval[szcol]: the lists of S as z values (same order)
-    int32_t vmin;              // smallest z value
-    uint32_t vspan;            // largest minus smallest z value
+    const int32_t* qbeg;       // batches: first x (= z) id of every query, else null
+    int32_t nq;
     const int32_t* deg_sy;
     const int32_t* hx;
     const int32_t* hy;
@@ -352,7 +351,8 @@ __global__ void light_warp_kernel(LightArgs A, const int32_t* queue, const Count
 // ------------------------------------------------------------ bucket class
 // One warp per light x with W_CAP < c <= CAP, deduplicated by an
 // order-preserving bucket sort: pass 1 counts the candidates per bucket of
-// the z values (bucket = (z - vmin) >> sh with vspan >> sh < nb, monotone),
+// the row's z value range (bucket = (z - vlo) >> sh with span >> sh < nb,
+// monotone; the range comes from the ends of the row's sorted lists),
 // pass 2 scatters them to their bucket's range, then every lane sorts and
 // deduplicates whole buckets (about 8 values each) by insertion, and the
 // buckets are written in order.
@@ -378,11 +378,27 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
             continue;
         }
         const uint32_t nb = min((uint32_t)NB, max(32u, next_pow2((n + 7) / 8)));
-        // bucket = (z - vmin) >> sh: monotone in z, and (vspan >> sh) < nb
-        const int sh = max(0, (32 - __clz(A.vspan)) - (31 - __clz(nb)));
         for (uint32_t k = lane; k < NB; k += 32) cnt[k] = 0;
-        __syncwarp();
         const int32_t e0 = A.rxoff[a], e1 = A.rxoff[a + 1];
+        // the row's value range from its sorted lists' first and last entries;
+        // bucket = (z - vlo) >> sh is monotone in z and (span >> sh) < nb
+        int32_t vlo = INT32_MAX, vhi = INT32_MIN;
+        for (int32_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t b = A.rycol[e];
+            const int32_t s0 = A.syoff[b], s1 = A.syoff[b + 1];
+            if (s1 > s0) {
+                vlo = min(vlo, A.szval[s0]);
+                vhi = max(vhi, A.szval[s1 - 1]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vlo = min(vlo, __shfl_xor_sync(0xffffffffu, vlo, o));
+            vhi = max(vhi, __shfl_xor_sync(0xffffffffu, vhi, o));
+        }
+        const uint32_t span = vhi >= vlo ? (uint32_t)vhi - (uint32_t)vlo : 0u;
+        const int sh = max(0, (32 - __clz(span)) - (31 - __clz(nb)));
+        __syncwarp();
         for (int32_t e = e0; e < e1; ++e) {
             const int32_t b = A.rycol[e];
             const int32_t s0 = A.syoff[b], L = A.syoff[b + 1] - s0;
@@ -392,7 +408,7 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
                 for (int u = 0; u < 4; ++u) zz[u] = (t0 + 32 * u < L) ? A.szval[s0 + t0 + 32 * u] : 0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (t0 + 32 * u < L) atomicAdd(&cnt[(uint32_t)(zz[u] - A.vmin) >> sh], 1u);
+                    if (t0 + 32 * u < L) atomicAdd(&cnt[((uint32_t)zz[u] - (uint32_t)vlo) >> sh], 1u);
             }
         }
         __syncwarp();
@@ -422,7 +438,7 @@ __global__ void light_bucket_kernel(LightArgs A, const int32_t* queue, const Cou
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (t0 + 32 * u < L) {
-                        const uint32_t p = atomicAdd(&cur[(uint32_t)(zz[u] - A.vmin) >> sh], 1u);
+                        const uint32_t p = atomicAdd(&cur[((uint32_t)zz[u] - (uint32_t)vlo) >> sh], 1u);
                         buf[p] = zz[u];
                     }
             }
@@ -715,8 +731,20 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
         unsigned long long base = 0;
         bool room = true;
         unsigned long long running = 0;
-        for (int64_t z0 = 0; z0 < A.nz; z0 += win_bits) {
-            const int64_t zend = min(A.nz, z0 + win_bits);
+        // the z ids a row can reach: its query's range in a batch (x and z ids
+        // of one query coincide), else the whole domain
+        int64_t zr0 = 0, zr1 = A.nz;
+        if (A.qbeg) {
+            int32_t lo = 0, hi = A.nq;          // last q with qbeg[q] <= a
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (A.qbeg[mid] <= a) lo = mid; else hi = mid;
+            }
+            zr0 = A.qbeg[lo];
+            zr1 = A.qbeg[lo + 1];
+        }
+        for (int64_t z0 = zr0; z0 < zr1; z0 += win_bits) {
+            const int64_t zend = min(zr1, z0 + win_bits);
             const int32_t nwords = (int32_t)((zend - z0 + 31) >> 5);
             const int32_t nsumm = (nwords + 31) >> 5;
             // rows with many neighbours (the hubs): each warp takes 32 neighbour
@@ -939,7 +967,8 @@ __global__ void szval_kernel(const int32_t* __restrict__ szcol, const int32_t* _
 }  // namespace
 
 void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightResult& lr,
-                     Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars) {
+                     Arena& ws, cudaStream_t st, uint32_t* d_status, int64_t* host_scalars,
+                     const int32_t* qbeg, int32_t nq) {
     (void)host_scalars;
     const int64_t nx = g.nx;
     lr.tmp_off = ws.get<int64_t>(nx + 1);
@@ -959,11 +988,6 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         nx, cand, p.hx, g.rxoff, g.rycol, g.syoff, p.w, g.nz, queues, lr.cnt, lr.tmp_off, ctr);
     JP_CHECK_LAUNCH();
     tend(TM_CLASSIFY);
-    if (g.nz > 0) {   // z ids are in value order: the first and last are the extremes
-        JP_CUDA_TRY(cudaMemcpyAsync(&ctr->vmin, g.zval, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-        JP_CUDA_TRY(cudaMemcpyAsync(&ctr->vmax, g.zval + g.nz - 1, sizeof(int32_t),
-                                    cudaMemcpyDeviceToDevice, st));
-    }
     Counters hc;
     JP_CUDA_TRY(cudaMemcpyAsync(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     JP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -990,8 +1014,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     A.syoff = g.syoff;
     A.szcol = g.szcol;
     A.szval = lr.szval;
-    A.vmin = hc.vmin;
-    A.vspan = (uint32_t)hc.vmax - (uint32_t)hc.vmin;
+    A.qbeg = qbeg;
+    A.nq = nq;
     A.deg_sy = g.deg_sy;
     A.hx = p.hx;
     A.hy = p.hy;
