@@ -917,7 +917,7 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 }
                 if (lane == 31) sw[warp] = inc;
                 __syncthreads();
-                const uint32_t v = sw[lane];
+                const uint32_t v = lane < BM_THREADS / 32 ? sw[lane] : 0u;
                 uint32_t before = lane < warp ? v : 0u;
                 tot = v;
 #pragma unroll
