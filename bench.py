@@ -152,7 +152,7 @@ KERNEL_SLOTS = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>",
                 7: "light_bucket_kernel<2048,256>", 8: "light_merge_kernel",
                 9: "light_bitmap_kernel", 11: "place_kernel"}
 # timer slot -> light class index of jp_stats.light_* arrays
-SLOT_CLASS = {6: (0,), 7: (1,), 8: (4, 5), 9: (3, 6)}
+SLOT_CLASS = {6: (0,), 7: (1,), 8: (4, 5, 7), 9: (3, 6)}
 
 
 def kernel_roofline(slot, st, peaks, peak_kind, ms):

@@ -99,7 +99,8 @@ typedef struct {
                                   (c <= 2048), 2 single list copied in place, 3 bitmap (larger c,
                                   and every heavy x), 4 and 5 merge of sorted lists (c <= 4096,
                                   c <= 8192), 6 bitmap hubs (>= 128 lists or >= 65536
-                                  candidates), 7 unused */
+                                  candidates), 7 merge of sorted lists (c <= 2048); the bucket
+                                  sort (1) keeps rows of c <= 2048 with more than 64 lists */
     int64_t light_cand[8];     /* candidates enumerated per light class */
     int64_t light_deg[8];      /* neighbour-list entries read per light class */
     double  ms_total;          /* host wall time of the call */

@@ -189,7 +189,8 @@ struct LightResult {
     int32_t* tmp = nullptr;
     int64_t tmp_cap = 0;
     int64_t candidates = 0;
-    // per class: warp sort, bucket sort, single-list copy, bitmap, merge 4096, merge 8192, hubs
+    // per class: warp sort, bucket sort, single-list copy, bitmap, merge 4096, merge 8192, hubs,
+    // merge 2048
     int64_t class_x[8] = {};      // x values
     int64_t class_cand[8] = {};   // candidates
     int64_t class_deg[8] = {};    // neighbour entries

@@ -15,10 +15,11 @@
 //   one list      a light x with a single neighbour list is already sorted
 //                 and distinct: the output pass copies S[b] in place
 //   c <= 256      a warp sorts the candidates in shared memory (bitonic)
-//   c <= 2048     a warp bucket-sorts them over the z domain (linear work)
 //   c <= 8192     (at most 64 lists) a block merges the lists, which are
-//                 already sorted, pairwise in shared memory (two buffer sizes,
-//                 4096 and 8192)
+//                 already sorted, pairwise in shared memory (three buffer
+//                 sizes: 2048, 4096 and 8192)
+//   c <= 2048     (more than 64 lists) a warp bucket-sorts them over the
+//                 row's z range (linear work)
 //   larger, and every heavy x: a block marks z in a shared-memory bitmap
 //                 over the z domain (windowed when the domain is larger than
 //                 shared memory) with a one-bit-per-word summary, so that
@@ -47,7 +48,8 @@ constexpr int BM_THREADS = 1024;
 constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
 constexpr int BM_WARP_PER_LIST = 128;    // rows with this many neighbours: warp per list
 
-enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, Q_MERGE = 4, Q_MERGE2 = 5, Q_HUB = 6, NQ = 7 };
+enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, Q_MERGE = 4, Q_MERGE2 = 5, Q_HUB = 6,
+       Q_MERGE0 = 7, NQ = 8 };
 constexpr int64_t HUB_CAND = 65536;      // bitmap rows with this many candidates are hubs
 
 struct Counters {
@@ -155,9 +157,10 @@ __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
             const bool heavy = hx[a] >= 0;
             const int32_t dg = rxoff[a + 1] - rxoff[a];
             c = (unsigned long long)cand[a];
-            if (!heavy && c > (unsigned long long)W2_CAP && c <= (unsigned long long)M2_CAP &&
+            if (!heavy && c > (unsigned long long)W_CAP && c <= (unsigned long long)M2_CAP &&
                 dg > 1 && dg <= M_MAXL) {
-                q = c <= (unsigned long long)M_CAP ? Q_MERGE : Q_MERGE2;
+                q = c <= (unsigned long long)W2_CAP ? Q_MERGE0
+                                                    : (c <= (unsigned long long)M_CAP ? Q_MERGE : Q_MERGE2);
                 ub = c;
             } else if (heavy || (c > (unsigned long long)W2_CAP && dg > 1)) {
                 q = (dg >= BM_WARP_PER_LIST || c >= (unsigned long long)HUB_CAND) ? Q_HUB : Q_BITMAP;
@@ -1052,9 +1055,10 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         JP_CHECK_LAUNCH();
         tend(TM_LIGHT_C2);
     }
-    if (hc.q[Q_MERGE] || hc.q[Q_MERGE2]) {
+    if (hc.q[Q_MERGE0] || hc.q[Q_MERGE] || hc.q[Q_MERGE2]) {
         // 2 CAP ints of shared memory per block: 32 KB (6 blocks per SM) and
         // 64 KB (3 blocks per SM)
+        const size_t sm0 = (size_t)2 * W2_CAP * sizeof(int32_t);   // 16 KB: 8 blocks per SM
         const size_t sm1 = (size_t)2 * M_CAP * sizeof(int32_t);
         const size_t sm2 = (size_t)2 * M2_CAP * sizeof(int32_t);
         static bool attrm = false;
@@ -1074,6 +1078,11 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         if (hc.q[Q_MERGE]) {
             light_merge_kernel<M_CAP><<<grid_for(hc.q[Q_MERGE], 1, 152 * 6), M_THREADS, sm1, st>>>(
                 A, queues + (int64_t)Q_MERGE * nx, ctr, Q_MERGE);
+            JP_CHECK_LAUNCH();
+        }
+        if (hc.q[Q_MERGE0]) {
+            light_merge_kernel<W2_CAP><<<grid_for(hc.q[Q_MERGE0], 1, 152 * 8), M_THREADS, sm0, st>>>(
+                A, queues + (int64_t)Q_MERGE0 * nx, ctr, Q_MERGE0);
             JP_CHECK_LAUNCH();
         }
         tend(TM_LIGHT_MERGE);

@@ -180,11 +180,23 @@ def _class_relation(seed):
         ys.append(rng.choice(low, int(rng.integers(2, 4)), replace=False))
         xs.append(np.full(len(ys[-1]), a))
     nx += 200
+    # 100 further y of small degree and 20 rows of 66-70 of them: more than 64
+    # lists with c <= 2048 (the warp bucket class)
+    small = np.arange(ny, ny + 100)
+    for a in range(nx, nx + 20):
+        ys.append(rng.choice(small, int(rng.integers(66, 71)), replace=False))
+        xs.append(np.full(len(ys[-1]), a))
+    nx += 20
+    for k, b in enumerate(small):        # five more tuples on each
+        ys.append(np.full(5, b))
+        xs.append(nx + 5 * k + np.arange(5))
+    nx += 5 * len(small)
+    ydeg = np.concatenate([ydeg, np.zeros(len(small), ydeg.dtype)])
     rx = np.concatenate(xs).astype(np.int32)
     ry = np.concatenate(ys).astype(np.int32)
     # top up every y to its degree with extra x values (they are light rows too)
-    have = np.bincount(ry, minlength=ny)
-    extra_y = np.repeat(np.arange(ny), np.maximum(ydeg - have, 0))
+    have = np.bincount(ry, minlength=len(ydeg))
+    extra_y = np.repeat(np.arange(len(ydeg)), np.maximum(ydeg - have, 0))
     extra_x = nx + np.arange(len(extra_y))
     rx = np.concatenate([rx, extra_x]).astype(np.int64)
     # x -> x * 2654435761 + 12345 (mod 2^32, as int32) is one-to-one: values spread
@@ -197,10 +209,10 @@ def _class_relation(seed):
 def test_every_light_class(ctx, oracle_mod, seed):
     rx, ry = _class_relation(seed)
     want = oracle_mod.two_path(rx, ry)
-    # all light: the warp, bucket, copy, bitmap, both merge and the hub classes are used
+    # all light: the warp, bucket, copy, bitmap, three merge and the hub classes are used
     assert_same(run(ctx, rx, ry, d1=10 ** 6, d2=10 ** 6), want)
     st = ctx.stats()
-    assert all(st["light_x"][q] > 0 for q in range(7)), st["light_x"]
+    assert all(st["light_x"][q] > 0 for q in range(8)), st["light_x"]
     # heavy x and heavy y mixed in
     for d1, d2 in [(200, 30), (60, 8), (350, 65)]:
         assert_same(run(ctx, rx, ry, d1=d1, d2=d2), want)
