@@ -79,7 +79,10 @@ void Arena::begin() {
     size_t held = 0;
     for (auto& c : chunks) held += c.size;
     const size_t need = peak;
-    if (chunks.size() > 1 || (held > ((size_t)1 << 30) && 2 * need < held)) {
+    // keep the chunks while they serve queries of this size (reallocating
+    // them would fragment the allocator's pool); give them back when they
+    // hold more than three times what the last query used
+    if (held > ((size_t)1 << 30) && 3 * need < held) {
         release_all();
         hint = need;
     }

@@ -55,9 +55,9 @@ struct Arena {
     size_t hint = 0;     // size of the next chunk to allocate (the last query's peak)
 
     void reset() { cur = 0; off = 0; used = 0; }
-    // Start of a query: keep at most one chunk, and give it back when it is
-    // much larger than the previous query needed, so that one large query
-    // does not pin its workspace for the context's lifetime.
+    // Start of a query: give the chunks back when they hold more than three
+    // times what the previous query used, so that one large query does not
+    // pin its workspace for the context's lifetime.
     void begin();
     void* raw_alloc(size_t bytes);
     void raw_free(void* p, size_t bytes);
