@@ -154,6 +154,26 @@ KERNEL_SLOTS = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>",
 # timer slot -> light class index of jp_stats.light_* arrays
 SLOT_CLASS = {6: (0,), 7: (1,), 8: (4, 5, 7), 9: (3, 6)}
 
+# DRAM bytes (read + write) of one launch, from one ncu capture of the bench
+# workload (profiles/light_bitmap_kernel_powerlaw_10m_dram.md); reported only
+# while the kernel's source file is the one that was captured
+MEASURED_TRAFFIC = {
+    "light_bitmap_kernel": {"bytes": 1540441344 + 5362752768, "workload": "two_path_powerlaw_10m",
+                            "source": "paper_2002_12459_gb300/csrc/jp_light.cu",
+                            "sha1": "b69b31a681b4a4a0740532911bfa9b85bb90e26d"},
+}
+
+
+def measured_traffic(kernel, workload):
+    import hashlib
+    m = MEASURED_TRAFFIC.get(kernel)
+    if not m or m["workload"] != workload:
+        return None
+    with open(os.path.join(ROOT, m["source"]), "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() != m["sha1"]:
+            return None
+    return m["bytes"]
+
 
 def kernel_roofline(slot, st, peaks, peak_kind, ms):
     """Algorithmic work of one launch of a kernel slot / its event-timed duration."""
@@ -167,10 +187,12 @@ def kernel_roofline(slot, st, peaks, peak_kind, ms):
                 "peak": fp8_burst, "unit": "TFLOP/s", "frac": ach / fp8_burst, "traffic": None,
                 "peak_source": f"{peak_kind} bf16 burst x 2 (fp8 nominal ratio)"}
     if slot == 11:
-        # read each list entry (4 B), gather its value (4 B), write the k
-        # output columns (4 B each); per row: offsets, list start, row values
+        # read each list entry (4 B), write the k output columns (4 B each),
+        # gather the value of each id of a bitmap row (4 B; the other lists
+        # hold values); per row: offsets, list start, row values
         k = st.get("k", 2)
-        byts = (8.0 + 4.0 * k) * out + 20.0 * st["dom_x"]
+        ids = min(out, st["light_cand"][3] + st["light_cand"][6])
+        byts = (4.0 + 4.0 * k) * out + 4.0 * ids + 20.0 * st["dom_x"]
     else:
         # candidates gathered (4 B), neighbour lists and per-x records read
         # (4 B each), distinct values written (bounded by the candidates)
@@ -183,10 +205,12 @@ def kernel_roofline(slot, st, peaks, peak_kind, ms):
             "peak_source": f"{peak_kind} hbm copy"}
 
 
-def roofline(st, peaks, peak_kind, ms_by_slot):
+def roofline(st, peaks, peak_kind, ms_by_slot, workload=None):
     """Roofline of the slowest single kernel of the step, and of every kernel."""
     per = {KERNEL_SLOTS[s]: kernel_roofline(s, st, peaks, peak_kind, ms_by_slot[s])
            for s in KERNEL_SLOTS if ms_by_slot.get(s, 0.0) > 0}
+    for name, r in per.items():
+        r["traffic"] = measured_traffic(name, workload) if workload else None
     slot = max(KERNEL_SLOTS, key=lambda s: ms_by_slot.get(s, 0.0))
     top = dict(per[KERNEL_SLOTS[slot]])
     return top, per
@@ -349,7 +373,7 @@ def run_ours(args, rank, world, local_rank):
         base = cpu_baseline(rx, ry)
 
     peaks, kind = load_peaks()
-    rl, rl_all = roofline(st, peaks, kind, slot_ms)
+    rl, rl_all = roofline(st, peaks, kind, slot_ms, args.workload)
     launches = sum(s["kernel_launches"] for s in stats)
     ctx.close()
     if rank != 0:
@@ -445,7 +469,7 @@ def run_star(args):
                 "sample": (f"x1 values {lo2}..{hi2} (251 of {len(x1)}), single-threaded C oracle "
                            f"incl. its sort of the three relations; {n} distinct triples in {secs:.2f}s")}
     peaks, kind = load_peaks()
-    rl, rl_all = roofline(st, peaks, kind, slot_ms)
+    rl, rl_all = roofline(st, peaks, kind, slot_ms, args.workload)
     launches = sum(s_["kernel_launches"] for s_ in stats)
     ctx.close()
     return {
