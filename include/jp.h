@@ -140,6 +140,13 @@ int jp_set_stream(jp_ctx* ctx, void* stream);
  * distinct (x, z) pairs, k = 2.  R->n + S->n must stay below 2^31. */
 int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out);
 
+/* Self-test of failure detection: a kernel waits, with the bounded wait every device-side
+ * wait of the library uses (the heavy product's mbarrier waits), on an mbarrier that nothing
+ * arrives at.  The wait runs out after wait_ns (1 .. 5e9), the kernel records the timeout in
+ * the context's status word and returns, and the call returns JP_ETIMEOUT; the context stays
+ * usable.  Any other return code means the mechanism failed. */
+int jp_selftest_wait(jp_ctx* ctx, int64_t wait_ns);
+
 /* Batch of two-path self-joins Q_q(x,z) = R_q(x,y), R_q(z,y), q = 0..nq-1, evaluated in
  * one pass of the pipeline (each pass one launch over all queries).  Every value is tagged
  * with its query ((query, value) pairs are dictionary-encoded), so the batch is the single

@@ -394,6 +394,20 @@ int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t*
     return run_two_path(ctx, all, nullptr, out, &b);
 }
 
+int jp_selftest_wait(jp_ctx* ctx, int64_t wait_ns) {
+    if (!ctx) return JP_EINVAL;
+    if (wait_ns < 1 || wait_ns > 5000000000LL) return fail(ctx, JP_EINVAL, "wait_ns out of range");
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
+        jp::wait_selftest(ctx->d_status, wait_ns, ctx->stream);
+        status_check(ctx);
+    } catch (const jp::Error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return fail(ctx, JP_ECUDA, "the self-test wait did not run out");
+}
+
 int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
     if (!ctx) return JP_EINVAL;
     if (!out) return fail(ctx, JP_EINVAL, "out is NULL");

@@ -71,17 +71,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false (and the status word gets ST_TIMEOUT) after WAIT_NS.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+// Bounded wait: false (and the status word gets ST_TIMEOUT) after ns nanoseconds.
+__device__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, uint32_t* status,
+                              unsigned long long ns) {
     if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > WAIT_NS) {
+        if (globaltimer() - t0 > ns) {
             atomicOr(status, ST_TIMEOUT);
             return false;
         }
     }
     return true;
+}
+
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status) {
+    return mbar_wait_for(bar, parity, status, WAIT_NS);
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at; the wait must run out after ns and leave ST_TIMEOUT.
+__global__ void wait_selftest_kernel(uint32_t* status, unsigned long long ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_for(&bar, 0, status, ns);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
@@ -317,6 +331,11 @@ CUtensorMap make_map(const uint8_t* base, int64_t rows, int64_t k_bytes, int box
 }
 
 }  // namespace
+
+void wait_selftest(uint32_t* d_status, int64_t ns, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(d_status, (unsigned long long)ns);
+    JP_CHECK_LAUNCH();
+}
 
 void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStream_t st) {
     h.present = (p.u > 0 && p.v > 0 && p.w > 0);

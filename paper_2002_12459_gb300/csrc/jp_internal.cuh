@@ -134,6 +134,9 @@ struct Heavy {
 void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStream_t st,
                  uint32_t* d_status, uint32_t* hist_host, int64_t* host_scalars);
 
+// A kernel whose bounded wait (the heavy product's) is made to run out after ns.
+void wait_selftest(uint32_t* d_status, int64_t ns, cudaStream_t st);
+
 // Batches of self-joins (jp_batch.cu): global ids of (query, value) pairs.
 struct BatchIds {
     int32_t* xg = nullptr;        // [n] global x id of every tuple

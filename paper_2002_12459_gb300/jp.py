@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
                                               ctypes.POINTER(jp_result),
                                               ctypes.POINTER(ctypes.c_int64)]
             lib.jp_two_path_batch.restype = i32
+            lib.jp_selftest_wait.argtypes = [vp, i64]
+            lib.jp_selftest_wait.restype = i32
             lib.jp_star.argtypes = [vp, i32, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
             lib.jp_star.restype = i32
             lib.jp_get_stats.argtypes = [vp, ctypes.POINTER(jp_stats)]
@@ -197,6 +199,12 @@ class Context:
                                       ctypes.byref(res))
         self._check(rc)
         return self._take(res)
+
+    def selftest_wait(self, wait_ns: int) -> int:
+        """Run the bounded-wait self-test; returns the library's code (JP_ETIMEOUT expected)."""
+        rc = self.lib.jp_selftest_wait(self.h, int(wait_ns))
+        self._torch.cuda.synchronize(self.device)
+        return rc
 
     def two_path_batch(self, x, y, qoff):
         """Batch of self-joins: query q is tuples [qoff[q], qoff[q+1]) of (x, y).
