@@ -219,7 +219,10 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         ctx->tm.begin(jp::TM_PACK);
         jp::heavy_pack(g, p, h, ctx->ws, st);
         ctx->tm.end(jp::TM_PACK);
-        jp::heavy_gemm(h, p, ctx->d_status, st, nullptr);
+        const int2* tiles = batch ? jp::batch_tile_ranges(p, h, bid.xq_begin, bid.yq_begin,
+                                                          batch->nq, ctx->ws, st)
+                                  : nullptr;
+        jp::heavy_gemm(h, p, ctx->d_status, st, tiles);
 
         jp::LightResult lr;
         jp::light_and_union(g, p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars,

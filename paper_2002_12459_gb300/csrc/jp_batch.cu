@@ -114,6 +114,7 @@ void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
     b.xg = ws.get<int32_t>(m);
     b.yg = ws.get<int32_t>(m);
     b.xq_begin = ws.get<int32_t>((size_t)nq + 1);
+    b.yq_begin = ws.get<int32_t>((size_t)nq + 1);
     if (n > 0) {
         tag_kernel<<<G(n), 256, 0, st>>>(x, y, n, qoff, nq, kx, ky);
         JP_CHECK_LAUNCH();
@@ -134,6 +135,9 @@ void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
         uint64_t* u0 = ws.get<uint64_t>(m);
         int64_t nyg = 0;
         uint64_t* uy = sorted_distinct(ky, u0, n, &nyg, ws, st, hist_host);
+        query_begin_kernel<<<grid_for((int64_t)nq + 1, 256, 152), 256, 0, st>>>(uy, nyg, nq,
+                                                                                b.yq_begin);
+        JP_CHECK_LAUNCH();
         // ky may now hold scratch: search the distinct keys with a fresh tag pass
         uint64_t* ky2 = (uy == ky) ? u0 : ky;
         tag_kernel<<<G(n), 256, 0, st>>>(x, y, n, qoff, nq, t1, ky2);
@@ -144,6 +148,7 @@ void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
         b.nxg = 0;
         b.xorig = ws.get<int32_t>(1);
         JP_CUDA_TRY(cudaMemsetAsync(b.xq_begin, 0, ((size_t)nq + 1) * sizeof(int32_t), st));
+        JP_CUDA_TRY(cudaMemsetAsync(b.yq_begin, 0, ((size_t)nq + 1) * sizeof(int32_t), st));
     }
 }
 

@@ -166,7 +166,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     heavy_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, int num_kb, uint32_t* __restrict__ G,
-                      int64_t g_stride, uint32_t* status) {
+                      int64_t g_stride, uint32_t* status, const int2* __restrict__ tiles) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -182,6 +182,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM;
     const int n0 = blockIdx.x * BN;
+    // K blocks of this tile: all of them, or (batches) those of the queries its
+    // rows and columns share; none shared: the tile's product is zero, written
+    // before any barrier or tensor memory is set up
+    int kb0 = 0, kb1 = num_kb;
+    if (tiles) {
+        const int2 t = tiles[(int64_t)blockIdx.y * gridDim.x + blockIdx.x];
+        kb0 = max(t.x, 0);
+        kb1 = min(t.y, num_kb);
+    }
+    if (kb0 >= kb1) {
+        if (threadIdx.x >= 64) {               // warps 2-5: one row each thread
+            uint32_t* grow = G + (int64_t)(m0 + (int)threadIdx.x - 64) * g_stride + (n0 >> 5);
+#pragma unroll
+            for (int j = 0; j < BN / 32; ++j) grow[j] = 0u;
+        }
+        return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -207,9 +224,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         int issued = 0;
-        for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        for (int kb = kb0; kb < kb1; ++kb) {
+            const int i = kb - kb0;                 // stage and phase count from the first block
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
             if (!mbar_wait(&empty[s], ph ^ 1u, status)) break;
             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
             tma_load_2d(sA + s * A_STAGE, &tmA, &full[s], kb * BK, m0);
@@ -217,15 +235,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             ++issued;
         }
         // drain: every issued load has landed before the CTA may exit
-        for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-            mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, status);
+        for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
+            mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u, status);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         bool ok = true;
-        int kb = 0;
-        for (; kb < num_kb; ++kb) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+        for (int kb = kb0; kb < kb1; ++kb) {
+            const int i = kb - kb0;
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
             if (!mbar_wait(&full[s], ph, status)) { ok = false; break; }
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + s * A_STAGE);
@@ -233,7 +251,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < BK / 32; ++k) {
                 mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC,
-                       (kb | k) != 0 ? 1u : 0u);
+                       (i | k) != 0 ? 1u : 0u);
             }
             mma_commit(&empty[s]);
         }
@@ -332,6 +350,71 @@ CUtensorMap make_map(const uint8_t* base, int64_t rows, int64_t k_bytes, int box
 
 }  // namespace
 
+namespace {
+
+// last q with begin[q] <= id
+__device__ __forceinline__ int32_t query_of(const int32_t* begin, int32_t nq, int32_t id) {
+    int32_t lo = 0, hi = nq;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (begin[mid] <= id) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// first i in [0, n) with ids[i] >= v (ids ascending), n if none
+__device__ __forceinline__ int32_t lower_id(const int32_t* ids, int32_t n, int32_t v) {
+    int32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (ids[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Heavy x (rows), heavy z (columns) and heavy y (K) are numbered in id order,
+// and ids are in query order, so a tile's rows belong to queries [qm0, qm1],
+// its columns to [qn0, qn1], and the queries they share own one contiguous
+// range of heavy y.
+__global__ void tile_range_kernel(const int32_t* __restrict__ hx_inv, int64_t u,
+                                  const int32_t* __restrict__ hz_inv, int64_t w,
+                                  const int32_t* __restrict__ hy_inv, int64_t v,
+                                  const int32_t* __restrict__ xq_begin,
+                                  const int32_t* __restrict__ yq_begin, int32_t nq, int gx,
+                                  int gy, int2* __restrict__ tiles) {
+    const int64_t nt = (int64_t)gx * gy;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t mi = t / gx, nj = t % gx;
+        const int64_t r0 = mi * BM, c0 = nj * BN;
+        int2 out = make_int2(0, 0);
+        if (r0 < u && c0 < w) {
+            const int64_t r1 = min(u, r0 + BM) - 1, c1 = min(w, c0 + BN) - 1;
+            const int32_t qa = max(query_of(xq_begin, nq, hx_inv[r0]), query_of(xq_begin, nq, hz_inv[c0]));
+            const int32_t qb = min(query_of(xq_begin, nq, hx_inv[r1]), query_of(xq_begin, nq, hz_inv[c1]));
+            if (qa <= qb) {
+                const int32_t k0 = lower_id(hy_inv, (int32_t)v, yq_begin[qa]);
+                const int32_t k1 = lower_id(hy_inv, (int32_t)v, yq_begin[qb + 1]);
+                if (k0 < k1) out = make_int2(k0 / BK, (k1 + BK - 1) / BK);
+            }
+        }
+        tiles[t] = out;
+    }
+}
+
+}  // namespace
+
+int2* batch_tile_ranges(const Partition& p, const Heavy& h, const int32_t* xq_begin,
+                        const int32_t* yq_begin, int32_t nq, Arena& ws, cudaStream_t st) {
+    if (!h.present) return nullptr;
+    const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
+    int2* tiles = ws.get<int2>((size_t)gx * gy);
+    tile_range_kernel<<<grid_for((int64_t)gx * gy, 256, 152 * 4), 256, 0, st>>>(
+        p.hx_inv, p.u, p.hz_inv, p.w, p.hy_inv, p.v, xq_begin, yq_begin, nq, gx, gy, tiles);
+    JP_CHECK_LAUNCH();
+    return tiles;
+}
+
 void wait_selftest(uint32_t* d_status, int64_t ns, cudaStream_t st) {
     wait_selftest_kernel<<<1, 32, 0, st>>>(d_status, (unsigned long long)ns);
     JP_CHECK_LAUNCH();
@@ -358,7 +441,7 @@ void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStr
 }
 
 void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
-                void* (*)()) {
+                const int2* tiles) {
     (void)p;
     if (!h.present) return;
     CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
@@ -373,7 +456,7 @@ void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t s
     dim3 grid((unsigned)(h.w_pad / BN), (unsigned)(h.u_pad / BM));
     tbegin(TM_GEMM);
     heavy_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(ma, mb, (int)(h.v_pad / BK), h.G,
-                                                              h.g_stride, d_status);
+                                                              h.g_stride, d_status, tiles);
     JP_CHECK_LAUNCH();
     tend(TM_GEMM);
 }

@@ -134,6 +134,12 @@ struct Heavy {
 void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStream_t st,
                  uint32_t* d_status, uint32_t* hist_host, int64_t* host_scalars);
 
+// Batches: for every tile of the heavy product, the range of K blocks [x, y)
+// shared by the queries of its rows and of its columns (empty when they share
+// none: the heavy block of a batch is block-diagonal by query).
+int2* batch_tile_ranges(const Partition& p, const Heavy& h, const int32_t* xq_begin,
+                        const int32_t* yq_begin, int32_t nq, Arena& ws, cudaStream_t st);
+
 // A kernel whose bounded wait (the heavy product's) is made to run out after ns.
 void wait_selftest(uint32_t* d_status, int64_t ns, cudaStream_t st);
 
@@ -144,6 +150,7 @@ struct BatchIds {
     int32_t* xorig = nullptr;     // [nxg] global x id -> value
     int64_t nxg = 0;
     int32_t* xq_begin = nullptr;  // [nq + 1] first global x id of every query (nxg at nq)
+    int32_t* yq_begin = nullptr;  // [nq + 1] first global y id of every query
 };
 void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
                   const int64_t* qoff_host, BatchIds& b, Arena& ws, cudaStream_t st,
@@ -176,8 +183,9 @@ void build_light_z_lists(const int32_t* syoff, const int32_t* szcol, Partition& 
 
 // Heavy part (jp_gemm.cu)
 void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStream_t st);
+// tiles: null, or (batches) the K-block range of every tile (batch_tile_ranges).
 void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
-                void* (*get_encode)());
+                const int2* tiles = nullptr);
 
 // Light part + union (jp_light.cu)
 // A row's list: tmp_off >= 0 is its offset in tmp, holding z values, or, with
