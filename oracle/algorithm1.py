@@ -12,7 +12,7 @@ two-path, thresholds Delta1, Delta2 >= 1 (Algorithm 1):
   4. M <- M1 x M2 (numpy int64 product, exact counts);
   5. T <- T union {(a, c) : M_ac > 0}.
 
-Readings taken where the paper is ambiguous (each listed in the design doc):
+Readings taken where the paper is ambiguous:
 
 * y heaviness.  The Section 3.1 text measures y in S for both relations,
   Algorithm 1 measures y in each relation's own degree; the worked example
