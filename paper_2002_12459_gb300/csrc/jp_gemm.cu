@@ -238,13 +238,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; ++i)
             mbar_wait(&full[i % STAGES], (uint32_t)(i / STAGES) & 1u, status);
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
-        bool ok = true;
+        // ---------------- MMA issuer (a wait that runs out has set ST_TIMEOUT)
         for (int kb = kb0; kb < kb1; ++kb) {
             const int i = kb - kb0;
             const int s = i % STAGES;
             const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph, status)) { ok = false; break; }
+            if (!mbar_wait(&full[s], ph, status)) break;
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + s * A_STAGE);
             const uint32_t b0 = smem_u32(sB + s * B_STAGE);
@@ -259,7 +258,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         // wait for every issued MMA before teardown (bounded)
         mma_commit(drain);
         mbar_wait(drain, 0, status);
-        (void)ok;
     } else if (warp >= 2) {
         // ---------------- epilogue: TMEM -> bits -> G
         const int q = warp & 3;                // TMEM lane quadrant of this warp
