@@ -183,9 +183,17 @@ def kernel_roofline(slot, st, peaks, peak_kind, ms):
     if slot == 4:
         flops = 2.0 * st["u"] * st["v"] * st["w"]
         ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": KERNEL_SLOTS[slot], "ms": ms, "bound": "tensor", "achieved": ach,
-                "peak": fp8_burst, "unit": "TFLOP/s", "frac": ach / fp8_burst, "traffic": None,
-                "peak_source": f"{peak_kind} bf16 burst x 2 (fp8 nominal ratio)"}
+        r = {"kernel": KERNEL_SLOTS[slot], "ms": ms, "bound": "tensor", "achieved": ach,
+             "peak": fp8_burst, "unit": "TFLOP/s", "frac": ach / fp8_burst, "traffic": None,
+             "peak_source": f"{peak_kind} bf16 burst x 2 (fp8 nominal ratio)"}
+        if peaks.get("fp8_tcgen05_tflops"):
+            # this GPU's own FP8 tcgen05 rate, measured in this run (jp_measure_peaks)
+            f8 = peaks["fp8_tcgen05_tflops"]
+            r.update(peak=f8, frac=ach / f8,
+                     peak_source="measured: tcgen05 kind::f8f6f4 128x256x32 issue loop, this run",
+                     frac_of_bf16_burst_x2=ach / fp8_burst,
+                     frac_of_int8_mma_sync=ach / peaks["int8_mma_sync_tflops"])
+        return r
     if slot == 11:
         # read each list entry (4 B), write the k output columns (4 B each),
         # gather the value of each id of a bitmap row (4 B; the other lists
@@ -274,6 +282,8 @@ def run_ours(args, rank, world, local_rank):
     dx = torch.from_numpy(rx).cuda()
     dy = torch.from_numpy(ry).cuda()
     ctx = jp.Context(local_rank)
+    tensor_peaks = ctx.measure_peaks()          # this GPU's FP8 tcgen05 and INT8 mma.sync rates
+    log(f"[bench] measured tensor peaks: {tensor_peaks}")
     ctx.set_threshold(args.mode, args.delta1, args.delta2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -373,6 +383,7 @@ def run_ours(args, rank, world, local_rank):
         base = cpu_baseline(rx, ry)
 
     peaks, kind = load_peaks()
+    peaks.update(tensor_peaks)
     rl, rl_all = roofline(st, peaks, kind, slot_ms, args.workload)
     launches = sum(s["kernel_launches"] for s in stats)
     ctx.close()
@@ -412,6 +423,7 @@ def run_star(args):
     log(f"[bench] workload {args.workload}: {len(rels)} x {len(rels[0][0])} tuples in {time.time() - t:.1f}s")
     drels = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in rels]
     ctx = jp.Context(0)
+    tensor_peaks = ctx.measure_peaks()
     ctx.set_threshold(args.mode, args.delta1, args.delta2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for i in range(args.warmup):
@@ -469,6 +481,7 @@ def run_star(args):
                 "sample": (f"x1 values {lo2}..{hi2} (251 of {len(x1)}), single-threaded C oracle "
                            f"incl. its sort of the three relations; {n} distinct triples in {secs:.2f}s")}
     peaks, kind = load_peaks()
+    peaks.update(tensor_peaks)
     rl, rl_all = roofline(st, peaks, kind, slot_ms, args.workload)
     launches = sum(s_["kernel_launches"] for s_ in stats)
     ctx.close()

@@ -140,6 +140,12 @@ int jp_set_stream(jp_ctx* ctx, void* stream);
  * distinct (x, z) pairs, k = 2.  R->n + S->n must stay below 2^31. */
 int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out);
 
+/* Measured dense tensor rates of this GPU, the denominators of the heavy product's roofline:
+ * *fp8_tflops from tcgen05 kind::f8f6f4 MMAs of the product's 128x256x32 shape on operands in
+ * shared memory (one CTA per SM, no loads), *int8_mma_sync_tflops from the legacy
+ * mma.sync m16n8k32 s8 path.  Takes about 50 ms. */
+int jp_measure_peaks(jp_ctx* ctx, double* fp8_tflops, double* int8_mma_sync_tflops);
+
 /* Self-test of failure detection: a kernel waits, with the bounded wait every device-side
  * wait of the library uses (the heavy product's mbarrier waits), on an mbarrier that nothing
  * arrives at.  The wait runs out after wait_ns (1 .. 5e9), the kernel records the timeout in

@@ -397,6 +397,22 @@ int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t*
     return run_two_path(ctx, all, nullptr, out, &b);
 }
 
+int jp_measure_peaks(jp_ctx* ctx, double* fp8_tflops, double* int8_mma_sync_tflops) {
+    if (!ctx || !fp8_tflops || !int8_mma_sync_tflops) return ctx ? fail(ctx, JP_EINVAL, "NULL argument") : JP_EINVAL;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        int sms = 0;
+        JP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        ctx->ws.begin();
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
+        jp::measure_peaks(sms, fp8_tflops, int8_mma_sync_tflops, ctx->d_status, ctx->ws, ctx->stream);
+        status_check(ctx);
+    } catch (const jp::Error& e) {
+        return fail(ctx, e.code, e.msg);
+    }
+    return JP_OK;
+}
+
 int jp_selftest_wait(jp_ctx* ctx, int64_t wait_ns) {
     if (!ctx) return JP_EINVAL;
     if (wait_ns < 1 || wait_ns > 5000000000LL) return fail(ctx, JP_EINVAL, "wait_ns out of range");

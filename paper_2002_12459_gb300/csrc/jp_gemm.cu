@@ -24,6 +24,7 @@ constexpr int BM = 128;           // rows of A per tile (heavy x)
 constexpr int BN = 256;           // rows of B per tile (heavy z)
 constexpr int BK = 128;           // bytes (= FP8 elements) of K per stage
 constexpr int STAGES = 4;
+constexpr int GROUP_M = 8;          // row tiles per group of the tile order
 constexpr int A_STAGE = BM * BK;  // 16 KB
 constexpr int B_STAGE = BN * BK;  // 32 KB
 constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
@@ -166,7 +167,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     heavy_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, int num_kb, uint32_t* __restrict__ G,
-                      int64_t g_stride, uint32_t* status, const int2* __restrict__ tiles) {
+                      int64_t g_stride, uint32_t* status, const int2* __restrict__ tiles, int gx,
+                      int gy) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -180,14 +182,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM;
-    const int n0 = blockIdx.x * BN;
+    // tile order: groups of GROUP_M row tiles, column tiles outer within a group,
+    // so that the CTAs resident at one time share a few row blocks of A and
+    // column blocks of B that fit in L2 (instead of streaming all of B again
+    // for every row block)
+    const int gid = blockIdx.x / (GROUP_M * gx);
+    const int first_m = gid * GROUP_M;
+    const int gsz = min(gy - first_m, GROUP_M);
+    const int in_group = blockIdx.x % (GROUP_M * gx);
+    const int mi = first_m + in_group % gsz;
+    const int nj = in_group / gsz;
+    const int m0 = mi * BM;
+    const int n0 = nj * BN;
     // K blocks of this tile: all of them, or (batches) those of the queries its
     // rows and columns share; none shared: the tile's product is zero, written
     // before any barrier or tensor memory is set up
     int kb0 = 0, kb1 = num_kb;
     if (tiles) {
-        const int2 t = tiles[(int64_t)blockIdx.y * gridDim.x + blockIdx.x];
+        const int2 t = tiles[(int64_t)mi * gx + nj];
         kb0 = max(t.x, 0);
         kb1 = min(t.y, num_kb);
     }
@@ -350,6 +362,81 @@ CUtensorMap make_map(const uint8_t* base, int64_t rows, int64_t k_bytes, int box
 
 namespace {
 
+// ---------------------------------------------------------------- peak rates
+// Dense FP8 tcgen05 rate: each CTA issues `iters` rounds of four 128x256x32
+// kind::f8f6f4 MMAs (the product kernel's shape) on operands held in shared
+// memory, with no loads, into one TMEM accumulator.
+__global__ void __launch_bounds__(64, 1) fp8_peak_kernel(int iters, uint32_t* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + A_STAGE;
+    uint64_t* done = reinterpret_cast<uint64_t*>(smem + A_STAGE + B_STAGE);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < (A_STAGE + B_STAGE) / 16; i += blockDim.x)
+        reinterpret_cast<int4*>(smem)[i] = make_int4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands seen by the MMA unit
+    if (threadIdx.x == 0) {
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+    if (warp == 1 && lane == 0) {
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < BK / 32; ++k)
+                mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC,
+                       (it | k) != 0 ? 1u : 0u);
+        }
+        mma_commit(done);
+        mbar_wait(done, 0, status);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Legacy INT8 tensor rate: every warp issues `iters` rounds of eight
+// independent mma.sync m16n8k32 s8 x s8 -> s32.
+__global__ void int8_mma_peak_kernel(int iters, int32_t* sink) {
+    uint32_t a0 = threadIdx.x, a1 = a0 * 3u, a2 = a0 * 5u, a3 = a0 * 7u, b0 = a0 ^ 0x55u,
+             b1 = a0 ^ 0xAAu;
+    int32_t c[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            asm volatile(
+                "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                "{%8,%9}, {%0,%1,%2,%3};"
+                : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    }
+    int32_t t = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += c[j][0] ^ c[j][1] ^ c[j][2] ^ c[j][3];
+    if (t == 0x5eed1234) sink[0] = t;                // keeps the loop
+}
+
 // last q with begin[q] <= id
 __device__ __forceinline__ int32_t query_of(const int32_t* begin, int32_t nq, int32_t id) {
     int32_t lo = 0, hi = nq;
@@ -402,6 +489,46 @@ __global__ void tile_range_kernel(const int32_t* __restrict__ hx_inv, int64_t u,
 
 }  // namespace
 
+void measure_peaks(int sms, double* fp8_tflops, double* int8_tflops, uint32_t* d_status,
+                   Arena& ws, cudaStream_t st) {
+    const size_t smem = (size_t)A_STAGE + B_STAGE + 1024 + 64;
+    static bool attr = false;
+    if (!attr) {
+        JP_CUDA_TRY(cudaFuncSetAttribute(fp8_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+        attr = true;
+    }
+    cudaEvent_t e0, e1;
+    JP_CUDA_TRY(cudaEventCreate(&e0));
+    JP_CUDA_TRY(cudaEventCreate(&e1));
+    float ms = 0;
+    // FP8: one CTA per SM, 20000 rounds of 4 MMAs (~ 40 ms at the nominal rate)
+    const int iters8 = 20000;
+    fp8_peak_kernel<<<sms, 64, smem, st>>>(64, d_status);       // warm-up
+    JP_CHECK_LAUNCH();
+    JP_CUDA_TRY(cudaEventRecord(e0, st));
+    fp8_peak_kernel<<<sms, 64, smem, st>>>(iters8, d_status);
+    JP_CHECK_LAUNCH();
+    JP_CUDA_TRY(cudaEventRecord(e1, st));
+    JP_CUDA_TRY(cudaEventSynchronize(e1));
+    JP_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *fp8_tflops = 2.0 * BM * BN * 32.0 * (BK / 32) * (double)iters8 * sms / (ms * 1e-3) / 1e12;
+    // INT8 mma.sync: 8 warps per block, 4 blocks per SM
+    int32_t* sink = ws.get<int32_t>(1);
+    const int iters = 4096, blocks = sms * 4, threads = 256;
+    int8_mma_peak_kernel<<<blocks, threads, 0, st>>>(16, sink);  // warm-up
+    JP_CHECK_LAUNCH();
+    JP_CUDA_TRY(cudaEventRecord(e0, st));
+    int8_mma_peak_kernel<<<blocks, threads, 0, st>>>(iters, sink);
+    JP_CHECK_LAUNCH();
+    JP_CUDA_TRY(cudaEventRecord(e1, st));
+    JP_CUDA_TRY(cudaEventSynchronize(e1));
+    JP_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *int8_tflops = 2.0 * 16 * 8 * 32 * 8.0 * iters * ((double)blocks * threads / 32) / (ms * 1e-3) / 1e12;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
 int2* batch_tile_ranges(const Partition& p, const Heavy& h, const int32_t* xq_begin,
                         const int32_t* yq_begin, int32_t nq, Arena& ws, cudaStream_t st) {
     if (!h.present) return nullptr;
@@ -451,10 +578,10 @@ void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t s
                                          (int)GEMM_SMEM));
         attr = true;
     }
-    dim3 grid((unsigned)(h.w_pad / BN), (unsigned)(h.u_pad / BM));
+    const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
     tbegin(TM_GEMM);
-    heavy_gemm_kernel<<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(ma, mb, (int)(h.v_pad / BK), h.G,
-                                                              h.g_stride, d_status, tiles);
+    heavy_gemm_kernel<<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
+        ma, mb, (int)(h.v_pad / BK), h.G, h.g_stride, d_status, tiles, gx, gy);
     JP_CHECK_LAUNCH();
     tend(TM_GEMM);
 }

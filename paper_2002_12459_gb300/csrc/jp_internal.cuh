@@ -140,6 +140,11 @@ void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStre
 int2* batch_tile_ranges(const Partition& p, const Heavy& h, const int32_t* xq_begin,
                         const int32_t* yq_begin, int32_t nq, Arena& ws, cudaStream_t st);
 
+// Measured dense tensor rates (TFLOP/s): tcgen05 FP8 MMAs of the product's
+// shape on shared-memory operands, and legacy INT8 mma.sync m16n8k32.
+void measure_peaks(int sms, double* fp8_tflops, double* int8_tflops, uint32_t* d_status,
+                   Arena& ws, cudaStream_t st);
+
 // A kernel whose bounded wait (the heavy product's) is made to run out after ns.
 void wait_selftest(uint32_t* d_status, int64_t ns, cudaStream_t st);
 

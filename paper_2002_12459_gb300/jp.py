@@ -93,6 +93,9 @@ def load(path: str = LIB_PATH):
             lib.jp_two_path_batch.restype = i32
             lib.jp_selftest_wait.argtypes = [vp, i64]
             lib.jp_selftest_wait.restype = i32
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.jp_measure_peaks.argtypes = [vp, dp, dp]
+            lib.jp_measure_peaks.restype = i32
             lib.jp_star.argtypes = [vp, i32, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
             lib.jp_star.restype = i32
             lib.jp_get_stats.argtypes = [vp, ctypes.POINTER(jp_stats)]
@@ -199,6 +202,12 @@ class Context:
                                       ctypes.byref(res))
         self._check(rc)
         return self._take(res)
+
+    def measure_peaks(self) -> dict:
+        """Measured dense tensor rates (TFLOP/s): tcgen05 FP8 and INT8 mma.sync."""
+        f8, i8 = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.jp_measure_peaks(self.h, ctypes.byref(f8), ctypes.byref(i8)))
+        return {"fp8_tcgen05_tflops": f8.value, "int8_mma_sync_tflops": i8.value}
 
     def selftest_wait(self, wait_ns: int) -> int:
         """Run the bounded-wait self-test; returns the library's code (JP_ETIMEOUT expected)."""

@@ -51,6 +51,9 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     lib.jp_selftest_wait.restype = ctypes.c_int
     lib.jp_selftest_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64]
     assert lib.jp_selftest_wait(None, 1000) == -1
+    lib.jp_measure_peaks.restype = ctypes.c_int
+    lib.jp_measure_peaks.argtypes = [ctypes.c_void_p] * 3
+    assert lib.jp_measure_peaks(None, None, None) == -1
     lib.jp_last_error.restype = ctypes.c_char_p
     lib.jp_last_error.argtypes = [ctypes.c_void_p]
     assert lib.jp_last_error(None) == b"NULL context"
