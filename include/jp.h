@@ -169,7 +169,11 @@ int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t*
                       jp_result* out, int64_t* out_off);
 
 /* Star query Q*_k (Section 2.1, Section 3.2) over rels[0..k-1], 2 <= k <= 8;
- * on success *out holds the sorted distinct k-tuples. */
+ * on success *out holds the sorted distinct k-tuples (k columns).  k = 2 is the two-path
+ * query with S = rels[1]; k = 3 runs the Section 3.2 algorithm factorised on (x1, x2); for
+ * k > 3 the relations R3..Rk are first grouped on y into one relation whose x is the id of a
+ * distinct tuple (a3, .., ak) sharing a y (JP_EUNSUPPORTED if that relation would hold 2^31
+ * or more tuples), the k = 3 algorithm runs on (R1, R2, it), and the ids are expanded. */
 int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out);
 
 /* Statistics of the last successful query. */

@@ -442,11 +442,10 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         out->k = 2;
         return rc;
     }
-    if (k > 3) return fail(ctx, JP_EUNSUPPORTED, "star queries are supported for k = 2 and k = 3");
     const auto t_start = std::chrono::steady_clock::now();
     void* block = nullptr;
     size_t block_bytes = 0;
-    out->k = 3;
+    out->k = k;
     try {
         JP_CUDA_TRY(cudaSetDevice(ctx->device));
         cudaStream_t st = ctx->stream;
@@ -457,11 +456,29 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         ctx->tm.st = st;
         jp::g_timer = &ctx->tm;
         ctx->tm.begin(jp::TM_TOTAL);
-        jp_rel rd[3];
-        for (int i = 0; i < 3; ++i) rd[i] = to_device(ctx, &rels[i]);
+        jp_rel rd[8];
+        for (int i = 0; i < k; ++i) rd[i] = to_device(ctx, &rels[i]);
 
-        jp::StarOut so;
         ctx->tm.begin(jp::TM_BUILD);
+        // k > 3: R3..Rk grouped on y from the right into one relation whose x
+        // is a group id; Q*_k is Q*_3 over (R1, R2, that relation), its third
+        // column expanded back through the groups' value tables
+        jp::PairRel levels[6];
+        jp::StarChain chain;
+        if (k > 3) {
+            jp_rel tail = rd[k - 1];
+            for (int i = k - 2; i >= 2; --i) {
+                jp::pair_relation(&rd[i], &tail, levels[i - 2], ctx->ws, st, ctx->hist_host);
+                tail = jp_rel{levels[i - 2].x, levels[i - 2].y, levels[i - 2].n};
+            }
+            rd[2] = tail;
+            chain.levels = k - 3;
+            for (int l = 0; l < k - 3; ++l) {
+                chain.gp[l] = levels[l].gp;
+                chain.gq[l] = levels[l].gq;
+            }
+        }
+        jp::StarOut so;
         jp::run_star3(rd, ctx->mode, ctx->d1, ctx->d2, so, ctx->ws, st, ctx->d_status,
                       ctx->hist_host);
         ctx->tm.end(jp::TM_BUILD);
@@ -479,14 +496,20 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         status_check(ctx);
         if (count > 0) {
             const size_t col_bytes = ((size_t)count * sizeof(int32_t) + 255) & ~(size_t)255;
-            block_bytes = 3 * col_bytes;
+            block_bytes = (size_t)k * col_bytes;
             block = ctx->ws.raw_alloc(block_bytes);
             if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < k; ++i)
                 out->col[i] = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(block) + i * col_bytes);
             ctx->tm.begin(jp::TM_PLACE);
             jp::output_write_rows(so.g, lr, out_off, count, so.row1, so.row2, out->col[0],
                                   out->col[1], out->col[2], st);
+            if (k > 3) {   // column 2 holds group ids: expand them in place into columns 2..k-1
+                int32_t** cols = ctx->ws.get<int32_t*>(8);
+                JP_CUDA_TRY(cudaMemcpyAsync(cols, out->col + 2, (size_t)(k - 2) * sizeof(int32_t*),
+                                            cudaMemcpyHostToDevice, st));
+                jp::star_expand(out->col[2], count, chain, cols, st);
+            }
             ctx->tm.end(jp::TM_PLACE);
         }
         ctx->tm.end(jp::TM_TOTAL);

@@ -247,6 +247,24 @@ struct StarOut {
 };
 void run_star3(const jp_rel* rels, int mode, int64_t fd1, int64_t fd2, StarOut& so, Arena& ws,
                cudaStream_t st, uint32_t* d_status, uint32_t* hist_host);
+// Star queries with k > 3 (jp_star.cu): the tail relations grouped on y.
+struct PairRel {
+    int32_t* x = nullptr;   // [n] group id of every tuple
+    int32_t* y = nullptr;   // [n] y value
+    int64_t n = 0;
+    int32_t* gp = nullptr;  // [ng] the pair's first value
+    int32_t* gq = nullptr;  // [ng] the pair's second value (the next level's group id)
+    int64_t ng = 0;
+};
+void pair_relation(const jp_rel* P, const jp_rel* Q, PairRel& out, Arena& ws, cudaStream_t st,
+                   uint32_t* hist_host);
+struct StarChain {
+    int levels = 0;                 // k - 3
+    const int32_t* gp[6] = {};
+    const int32_t* gq[6] = {};
+};
+void star_expand(const int32_t* g3, int64_t n, const StarChain& chain, int32_t* const* cols_dev,
+                 cudaStream_t st);
 // Integer (Delta1, Delta2) minimising the Section 3.2 star cost on a log grid.
 void star_thresholds(int64_t N, double out_est, int k, int64_t* d1, int64_t* d2);
 

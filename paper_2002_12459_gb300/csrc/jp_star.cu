@@ -325,6 +325,54 @@ double star_cost(double N, double OUT, double d1, double d2, int k) {
     return N * std::pow(d1, k - 1) + OUT * d2 + U * V * W / beta;
 }
 
+// ---- star queries with k > 3: the tail relations grouped on y
+// triples per y of two relations P, Q: degP(b) * degQ(b)
+__global__ void pair_count_kernel(const int32_t* dp, const int32_t* dq, int64_t ny, int64_t* cnt) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ny;
+         b += (int64_t)gridDim.x * blockDim.x)
+        cnt[b] = (int64_t)dp[b] * dq[b];
+}
+
+// warp per y: key (p | q | b) for every p in P[b] and q in Q[b]
+__global__ void pair_fill_kernel(int64_t ny, const int32_t* poff, const int32_t* pcol,
+                                 const int32_t* qoff, const int32_t* qcol, const int64_t* toff,
+                                 int shp, int shq, uint64_t* keys) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = warp; b < ny; b += nwarps) {
+        const int32_t p0 = poff[b], dp = poff[b + 1] - p0;
+        const int32_t q0 = qoff[b], dq = qoff[b + 1] - q0;
+        const int64_t n = (int64_t)dp * dq, o = toff[b];
+        for (int64_t t = lane; t < n; t += 32) {
+            const int64_t i = t / dq, j = t - i * dq;
+            keys[o + t] = ((uint64_t)pcol[p0 + i] << shp) | ((uint64_t)qcol[q0 + j] << shq) |
+                          (uint64_t)b;
+        }
+    }
+}
+
+// one tuple (g, y value) per sorted triple; the pair's values at its first
+// triple.  gid is the exclusive scan of the group-start flags, so a triple
+// after its group's first one has gid = g + 1.
+__global__ void pair_emit_kernel(const uint64_t* keys, int64_t n, const uint32_t* gid, int shp,
+                                 int shq, uint64_t mq, uint64_t my, const int32_t* pval,
+                                 const int32_t* qval, const int32_t* yval, int32_t* gx,
+                                 int32_t* gy, int32_t* gp, int32_t* gq) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        const bool start = i == 0 || (k >> shq) != (keys[i - 1] >> shq);
+        const uint32_t g = start ? gid[i] : gid[i] - 1u;
+        if (start) {
+            gp[g] = pval[k >> shp];
+            gq[g] = qval[(k >> shq) & mq];
+        }
+        gx[i] = (int32_t)g;
+        gy[i] = yval[k & my];
+    }
+}
+
 }  // namespace
 
 // Minimiser of the star cost over a log-spaced grid of integer thresholds.
@@ -525,6 +573,87 @@ void run_star3(const jp_rel* rels, int mode, int64_t fd1, int64_t fd2, StarOut& 
         JP_CHECK_LAUNCH();
     }
     (void)d_status;
+}
+
+// The star's tail grouped on y: one tuple (g, b) per (a_p, a_q, b) with
+// (a_p, b) in P and (a_q, b) in Q, g numbering the distinct pairs (a_p, a_q) in
+// value order (so that tuples of g compare as the pairs do); gp[g], gq[g] hold
+// the pair's values.  Q*_k with k > 3 is Q*_3 over R1, R2 and the tail
+// R3..Rk grouped this way from the right (Section 3.2 groups the star's
+// variables the same way for its product).
+void pair_relation(const jp_rel* P, const jp_rel* Q, PairRel& out, Arena& ws, cudaStream_t st,
+                   uint32_t* hist_host) {
+    int32_t* yval = nullptr;
+    const int64_t ny = make_dict(P->y, P->n, &yval, ws, st, hist_host);
+    ByY bp, bq;
+    index_by_y(P, yval, ny, bp, ws, st, hist_host);
+    index_by_y(Q, yval, ny, bq, ws, st, hist_host);
+    int64_t* cnt = ws.get<int64_t>(ny + 1);
+    int64_t* toff = ws.get<int64_t>(ny + 1);
+    int64_t* d_tot = ws.get<int64_t>(1);
+    if (ny > 0) {
+        pair_count_kernel<<<G(ny), 256, 0, st>>>(bp.degy, bq.degy, ny, cnt);
+        JP_CHECK_LAUNCH();
+    }
+    scan_i64(cnt, toff, ny, d_tot, ws, st);
+    const int64_t n = ny > 0 ? read1(d_tot, st) : 0;
+    if (n >= ((int64_t)1 << 31))
+        throw Error{JP_EUNSUPPORTED, "a grouped star tail would hold 2^31 or more tuples"};
+    const int shq = bits_for(ny), shp = shq + bits_for(bq.nx);
+    if (shp + bits_for(bp.nx) > 64)
+        throw Error{JP_EUNSUPPORTED, "grouped star tail keys need more than 64 bits"};
+    out.n = n;
+    out.x = ws.get<int32_t>(n + 1);
+    out.y = ws.get<int32_t>(n + 1);
+    out.ng = 0;
+    if (n == 0) {
+        out.gp = ws.get<int32_t>(1);
+        out.gq = ws.get<int32_t>(1);
+        return;
+    }
+    uint64_t* k0 = ws.get<uint64_t>(n);
+    uint64_t* k1 = ws.get<uint64_t>(n);
+    pair_fill_kernel<<<grid_for(ny * 32, 256, 152 * 16), 256, 0, st>>>(
+        ny, bp.off, bp.col, bq.off, bq.col, toff, shp, shq, k0);
+    JP_CHECK_LAUNCH();
+    uint64_t* ks = radix_sort_u64(k0, k1, n, ws, st, hist_host);
+    uint32_t* flag = ws.get<uint32_t>(n);
+    uint32_t* gid = ws.get<uint32_t>(n);
+    uint32_t* d_ng = ws.get<uint32_t>(1);
+    run_start_kernel<<<G(n), 256, 0, st>>>(ks, n, shq, flag);
+    JP_CHECK_LAUNCH();
+    scan_u32(flag, gid, n, d_ng, ws, st);
+    out.ng = read1(d_ng, st);
+    out.gp = ws.get<int32_t>(out.ng + 1);
+    out.gq = ws.get<int32_t>(out.ng + 1);
+    pair_emit_kernel<<<G(n), 256, 0, st>>>(ks, n, gid, shp, shq, ((uint64_t)1 << (shp - shq)) - 1,
+                                           ((uint64_t)1 << shq) - 1, bp.xval, bq.xval, yval,
+                                           out.x, out.y, out.gp, out.gq);
+    JP_CHECK_LAUNCH();
+}
+
+namespace {
+// columns 2.. of a star result from the grouped third column: follow the
+// chain of pair tables (gp: the level's value, gq: the next level's group id,
+// or the last relation's value at the last level)
+__global__ void expand_kernel(const int32_t* g3, int64_t n, StarChain chain, int32_t* const* cols) {
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int32_t g = g3[o];
+        for (int l = 0; l < chain.levels; ++l) {
+            cols[l][o] = chain.gp[l][g];
+            g = chain.gq[l][g];
+        }
+        cols[chain.levels][o] = g;
+    }
+}
+}  // namespace
+
+void star_expand(const int32_t* g3, int64_t n, const StarChain& chain, int32_t* const* cols_dev,
+                 cudaStream_t st) {
+    if (n <= 0) return;
+    expand_kernel<<<G(n), 256, 0, st>>>(g3, n, chain, cols_dev);
+    JP_CHECK_LAUNCH();
 }
 
 }  // namespace jp

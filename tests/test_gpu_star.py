@@ -109,9 +109,29 @@ def test_star_limits_and_empty(ctx):
     got = run(ctx, [(e, e)] * 3)
     assert all(len(c) == 0 for c in got)
     one = (np.array([1], np.int32), np.array([2], np.int32))
+    assert [c.tolist() for c in run(ctx, [one] * 4)] == [[1]] * 4
     with pytest.raises(jp.JPError) as ei:
-        run(ctx, [one] * 4)
-    assert ei.value.code == jp.JP_EUNSUPPORTED
+        run(ctx, [one] * 9)
+    assert ei.value.code == jp.JP_EINVAL
+    # k = 5 with one relation sharing no y with the others: empty
+    got = run(ctx, [one, one, one, (np.array([1], np.int32), np.array([3], np.int32)), one])
+    assert len(got) == 5 and all(len(c) == 0 for c in got)
     # relations sharing no y: empty result
     got = run(ctx, [one, (np.array([1], np.int32), np.array([3], np.int32)), one])
     assert all(len(c) == 0 for c in got)
+
+
+@pytest.mark.parametrize("k,seed", [(4, 0), (4, 1), (5, 2), (6, 3), (7, 4)])
+def test_star_k_above_3(ctx, oracle_mod, k, seed):
+    # the tail R3..Rk is grouped on y (pairs of relations, from the right) and
+    # Q*_k answered as Q*_3; small shared y domain so that every y joins
+    rng = np.random.default_rng(seed)
+    n = {4: 400, 5: 200, 6: 110, 7: 80}[k]
+    rels = [rel(rng, n, 60 + 7 * i, 25, -30 * (i % 2), 0, skew=0.5) for i in range(k)]
+    want = oracle_mod.star(rels)
+    assert len(want[0]) > 0
+    for mode, d1, d2 in [("fixed", 1, 1), ("fixed", 3, 2), ("fixed", 10 ** 6, 10 ** 6),
+                         ("cost_model", 1, 1)]:
+        got = run(ctx, rels, mode, d1, d2)
+        assert len(got) == k
+        same(got, want)
