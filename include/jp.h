@@ -113,6 +113,9 @@ typedef struct {
     int64_t learned_judged;    /* JP_LEARNED only: 1 the model's thresholds were used, 2 the cost
                                   model judged them too costly (modelled cost above 3 x that of
                                   Algorithm 3's thresholds) and Algorithm 3's were used; else 0 */
+    int64_t filter_pairs;      /* jp_two_path_filter only: distinct candidate pairs of T */
+    int64_t filter_query_out;  /* jp_two_path_filter only: |OUT| of the query on the reduced R and S
+                                  (out_count is then the number of pairs of T answered) */
 } jp_stats;
 
 typedef void* (*jp_alloc_fn)(size_t bytes, void* stream, void* user);
@@ -167,6 +170,20 @@ int jp_selftest_wait(jp_ctx* ctx, int64_t wait_ns);
  * Errors as jp_two_path; JP_EINVAL for bad offsets. */
 int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t* qoff,
                       jp_result* out, int64_t* out_off);
+
+/* Boolean set intersection queries in one batch (Section 3.3): every candidate pair (a, b) of
+ * T asks whether R(a, .) and S(b, .) share a y; the batch is the query
+ * Q_batch(x,z) = R(x,y), S(z,y), T(x,z).  As in the paper's experiments, R is reduced to the
+ * tuples whose x occurs in T and S to those whose z occurs in T, the two-path query runs on the
+ * reduced relations (Algorithm 1, the context's threshold mode), and its output is intersected
+ * with T.
+ *   T      the candidate pairs: T->x holds the a (x) values, T->y the b (z) values; device or
+ *          host columns as R; duplicates allowed; T->n < 2^31;
+ *   S      NULL means S = R;
+ *   out    the sorted distinct pairs of T whose sets intersect (k = 2).
+ * Errors as jp_two_path; JP_EINVAL when T is NULL. */
+int jp_two_path_filter(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, const jp_rel* T,
+                       jp_result* out);
 
 /* Star query Q*_k (Section 2.1, Section 3.2) over rels[0..k-1], 2 <= k <= 8;
  * on success *out holds the sorted distinct k-tuples (k columns).  k = 2 is the two-path

@@ -17,6 +17,10 @@ Contents:
 * ``algorithm1``: Algorithm 1 step by step in the paper's order (partition,
   light join, heavy matrices, matrix product, union), used to pin the worked
   example's matrices and the heavy dimensions.
+* ``bsi`` / ``brute_bsi``: the batch of boolean set intersection queries of
+  Section 3.3, Q_batch(x,z) = R(x,y), S(z,y), T(x,z), as the three-way join
+  followed by the projection on (x, z) (numpy), and as a pure-Python loop over
+  T for tiny inputs.
 * ``cost_model``: the threshold formulas (Section 3.1 closed forms, the
   Section 3.2 star cost, the Section 5 output estimate and Algorithm 3).
 """
@@ -36,7 +40,7 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "two_path", "star", "two_path_row", "brute_two_path",
-           "brute_star", "normalise"]
+           "brute_star", "normalise", "bsi", "brute_bsi"]
 
 
 def build(force: bool = False) -> str:
@@ -206,3 +210,53 @@ def normalise(x, y):
     ux = (key >> 32).astype(np.int32)
     uy = (key & 0xFFFFFFFF).astype(np.uint32).astype(np.int32)
     return ux, uy
+
+
+def _pair_keys(a, b) -> np.ndarray:
+    """int64 keys ordering pairs of int32 lexicographically (signed)."""
+    return (np.asarray(a, np.int64) << 32) | (np.asarray(b, np.int64) - I32_MIN)
+
+
+def bsi(rx, ry, tx, tz, sz=None, sy=None):
+    """Sorted distinct (a, b) of Q_batch(x,z) = R(x,y), S(z,y), T(x,z) (Section 3.3).
+
+    The join of T with R on x gives the triples (a, b, y); those whose (b, y)
+    is a tuple of S survive; the result is their projection on (a, b).
+    """
+    if sz is None:
+        sz, sy = rx, ry
+    rx, ry = normalise(rx, ry)
+    sz, sy = normalise(sz, sy)
+    tk = np.unique(_pair_keys(tx, tz))
+    ta = (tk >> 32).astype(np.int32)
+    tb = ((tk & 0xFFFFFFFF) + I32_MIN).astype(np.int32)
+    if len(tk) == 0 or len(rx) == 0 or len(sz) == 0:
+        return np.empty(0, np.int32), np.empty(0, np.int32)
+    # T join R on x: R is sorted by x, so a's tuples are one range
+    lo = np.searchsorted(rx, ta, "left")
+    hi = np.searchsorted(rx, ta, "right")
+    deg = hi - lo
+    pair = np.repeat(np.arange(len(tk)), deg)
+    start = np.repeat(lo - np.concatenate(([0], np.cumsum(deg)[:-1])), deg)
+    y = ry[np.arange(len(pair)) + start]
+    # semi-join of the triples with S on (z, y)
+    skeys = np.sort(_pair_keys(sz, sy))
+    k = _pair_keys(tb[pair], y)
+    at = np.minimum(np.searchsorted(skeys, k), len(skeys) - 1)
+    hit = np.unique(pair[skeys[at] == k])
+    return ta[hit], tb[hit]
+
+
+def brute_bsi(rx, ry, tx, tz, sz=None, sy=None):
+    """Pure-Python loop over the distinct pairs of T: tiny inputs only."""
+    if sz is None:
+        sz, sy = rx, ry
+    R = set(zip(map(int, rx), map(int, ry)))
+    S = set(zip(map(int, sz), map(int, sy)))
+    out = []
+    for a, b in sorted(set(zip(map(int, tx), map(int, tz)))):
+        ya = {y for x, y in R if x == a}
+        yb = {y for z, y in S if z == b}
+        if ya & yb:
+            out.append((a, b))
+    return out

@@ -163,8 +163,13 @@ struct BatchArgs {
 // The two-path pipeline.  With a batch, R holds the queries' tuples one after
 // another (batch->qoff) and is a self-join per query; its values are first
 // encoded to (query, value) ids, and the output maps them back.
+//
+// With a candidate set T (the Section 3.3 batch of boolean set intersection
+// queries), R and S are first reduced to T's x and z values, the pipeline
+// answers the reduced query into the workspace, and the result is the pairs of
+// T found in that output.
 int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
-                 const BatchArgs* batch) {
+                 const BatchArgs* batch, const jp_rel* T = nullptr) {
     if (!ctx) return JP_EINVAL;
     if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
     std::memset(out, 0, sizeof(*out));
@@ -173,6 +178,7 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
     if (rc) return rc;
     if (S && (rc = check_rel(ctx, S, "S"))) return rc;
     if (S && R->n + S->n >= ((int64_t)1 << 31)) return fail(ctx, JP_EUNSUPPORTED, "R and S together hold 2^31 or more tuples");
+    if (T && (rc = check_rel(ctx, T, "T"))) return rc;
     const auto t_start = std::chrono::steady_clock::now();
     void* block = nullptr;
     size_t block_bytes = 0;
@@ -189,7 +195,14 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         jp_rel Rd = to_device(ctx, R);
         jp_rel Sd;
         if (S) Sd = to_device(ctx, S);
-        const bool self = (S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n);
+        jp::FilterState fs;
+        if (T) {
+            const jp_rel Td = to_device(ctx, T);
+            jp::filter_reduce(Rd, S ? Sd : Rd, Td, fs, ctx->ws, st, ctx->hist_host);
+            Rd = fs.R;
+            Sd = fs.S;
+        }
+        const bool self = !T && ((S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n));
         jp::BatchIds bid;
         if (batch) {
             jp::batch_encode(Rd.x, Rd.y, Rd.n, batch->nq, batch->qoff, bid, ctx->ws, st,
@@ -233,19 +246,30 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         const int64_t count = jp::output_count(g, lr, out_off, ctx->ws, st, ctx->host_scalars);
         ctx->tm.end(jp::TM_COUNT);
         status_check(ctx);
-        if (count > 0) {
-            block_bytes = (size_t)count * 2 * sizeof(int32_t) + 512;
+        int64_t result_count = count;
+        if (T) {
+            int32_t* qx = ctx->ws.get<int32_t>(count + 1);
+            int32_t* qz = ctx->ws.get<int32_t>(count + 1);
+            ctx->tm.begin(jp::TM_PLACE);
+            if (count > 0) jp::output_write(g, lr, out_off, count, qx, qz, st);
+            ctx->tm.end(jp::TM_PLACE);
+            result_count = jp::filter_find(fs, qx, qz, count, ctx->ws, st);
+        }
+        if (result_count > 0) {
+            block_bytes = (size_t)result_count * 2 * sizeof(int32_t) + 512;
             block = ctx->ws.raw_alloc(block_bytes);
             if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
             int32_t* ox = reinterpret_cast<int32_t*>(block);
             int32_t* oz = reinterpret_cast<int32_t*>(
-                reinterpret_cast<char*>(block) + (((size_t)count * sizeof(int32_t) + 255) & ~(size_t)255));
-            ctx->tm.begin(jp::TM_PLACE);
-            if (batch)
+                reinterpret_cast<char*>(block) + (((size_t)result_count * sizeof(int32_t) + 255) & ~(size_t)255));
+            if (!T) ctx->tm.begin(jp::TM_PLACE);
+            if (T)
+                jp::filter_emit(fs, ox, oz, st);
+            else if (batch)
                 jp::output_write_mapped(g, lr, out_off, count, bid.xorig, ox, oz, st);
             else
                 jp::output_write(g, lr, out_off, count, ox, oz, st);
-            ctx->tm.end(jp::TM_PLACE);
+            if (!T) ctx->tm.end(jp::TM_PLACE);
             out->col[0] = ox;
             out->col[1] = oz;
         }
@@ -253,7 +277,7 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         ctx->tm.end(jp::TM_TOTAL);
         status_check(ctx);
         jp::g_timer = nullptr;
-        out->count = count;
+        out->count = result_count;
         out->_block = block;
         out->_bytes = block_bytes;
 
@@ -273,8 +297,10 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         s.v = p.v;
         s.w = p.w;
         s.light_candidates = lr.candidates;
-        s.out_count = count;
+        s.out_count = result_count;
         s.learned_judged = judged;
+        s.filter_pairs = T ? fs.nt : 0;
+        s.filter_query_out = T ? count : 0;
         s.kernel_launches = jp::g_launches - launches0;
         for (int q = 0; q < 8; ++q) {
             s.light_x[q] = lr.class_x[q];
@@ -395,6 +421,13 @@ int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t*
         if (qoff[q + 1] < qoff[q]) return fail(ctx, JP_EINVAL, "query offsets must not decrease");
     const BatchArgs b{nq, qoff, out_off};
     return run_two_path(ctx, all, nullptr, out, &b);
+}
+
+int jp_two_path_filter(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, const jp_rel* T,
+                       jp_result* out) {
+    if (!ctx) return JP_EINVAL;
+    if (!T) return fail(ctx, JP_EINVAL, "T is NULL");
+    return run_two_path(ctx, R, S, out, nullptr, T);
 }
 
 int jp_measure_peaks(jp_ctx* ctx, double* fp8_tflops, double* int8_mma_sync_tflops) {

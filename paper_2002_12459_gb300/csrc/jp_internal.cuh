@@ -164,6 +164,23 @@ void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
 void batch_offsets(const int64_t* out_off, int64_t nx, int64_t count, const BatchIds& b,
                    int32_t nq, int64_t* host_offsets, Arena& ws, cudaStream_t st);
 
+// Boolean set intersection in batches (jp_filter.cu, Section 3.3): the
+// candidate pairs T and R, S reduced to T's x and z values.
+struct FilterState {
+    uint64_t* tkeys = nullptr;    // [nt] sorted distinct pairs of T, (x ^ 2^31) << 32 | (z ^ 2^31)
+    int64_t nt = 0;
+    jp_rel R{}, S{};              // R restricted to T's x values, S to T's z values
+    uint32_t* flag = nullptr;     // [nt] pair found in the query's output (filter_find)
+    uint32_t* pos = nullptr;      // [nt] exclusive scan of flag
+};
+void filter_reduce(const jp_rel& R, const jp_rel& S, const jp_rel& T, FilterState& fs, Arena& ws,
+                   cudaStream_t st, uint32_t* hist_host);
+// Marks the pairs of T present in the sorted output (ox, oz)[0..no); returns how many.
+int64_t filter_find(FilterState& fs, const int32_t* ox, const int32_t* oz, int64_t no, Arena& ws,
+                    cudaStream_t st);
+// Writes the marked pairs, in order, to (px, pz).
+void filter_emit(const FilterState& fs, int32_t* px, int32_t* pz, cudaStream_t st);
+
 // Threshold selection (jp_select.cu)
 double out_estimate(double dom_x, double out_join, double N);
 // *judged (JP_LEARNED): 1 the model's thresholds kept, 2 replaced by Algorithm 3's.

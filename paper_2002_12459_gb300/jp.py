@@ -55,7 +55,8 @@ class jp_stats(ctypes.Structure):
                 ("light_x", ctypes.c_int64 * 8), ("light_cand", ctypes.c_int64 * 8),
                 ("light_deg", ctypes.c_int64 * 8),
                 ("ms_total", ctypes.c_double),
-                ("ms_pass", ctypes.c_double * 16), ("learned_judged", ctypes.c_int64)]
+                ("ms_pass", ctypes.c_double * 16), ("learned_judged", ctypes.c_int64),
+                ("filter_pairs", ctypes.c_int64), ("filter_query_out", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -91,6 +92,9 @@ def load(path: str = LIB_PATH):
                                               ctypes.POINTER(jp_result),
                                               ctypes.POINTER(ctypes.c_int64)]
             lib.jp_two_path_batch.restype = i32
+            lib.jp_two_path_filter.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
+                                               ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
+            lib.jp_two_path_filter.restype = i32
             lib.jp_selftest_wait.argtypes = [vp, i64]
             lib.jp_selftest_wait.restype = i32
             dp = ctypes.POINTER(ctypes.c_double)
@@ -200,6 +204,19 @@ class Context:
         with self._torch.cuda.stream(self.stream):
             rc = self.lib.jp_two_path(self.h, ctypes.byref(R), ctypes.byref(S) if S else None,
                                       ctypes.byref(res))
+        self._check(rc)
+        return self._take(res)
+
+    def two_path_filter(self, tx, tz, rx, ry, sz=None, sy=None):
+        """Pairs (a, b) of T = (tx, tz) with R(a, y), S(b, y) for some y: sorted, distinct."""
+        R = _rel_of(rx, ry)
+        S = _rel_of(sz, sy) if sz is not None else None
+        T = _rel_of(tx, tz)
+        res = jp_result()
+        with self._torch.cuda.stream(self.stream):
+            rc = self.lib.jp_two_path_filter(self.h, ctypes.byref(R),
+                                             ctypes.byref(S) if S else None, ctypes.byref(T),
+                                             ctypes.byref(res))
         self._check(rc)
         return self._take(res)
 

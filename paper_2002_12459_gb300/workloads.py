@@ -204,6 +204,29 @@ def random_small_relation(rng, n: int, dom_x: int, dom_y: int, offset_x: int = 0
     return ((x + offset_x).astype(np.int32), (y + offset_y).astype(np.int32))
 
 
+def candidate_pairs(x_vals: np.ndarray, z_vals: np.ndarray, count: int, seed: int = 0,
+                    absent: float = 0.0):
+    """Candidate pairs (a, b) for a batch of boolean set intersection requests.
+
+    ``a`` is drawn uniformly from ``x_vals`` and ``b`` from ``z_vals`` (with
+    replacement, so pairs repeat); a fraction ``absent`` of the pairs names,
+    on one side, a value outside the given ones.
+    """
+    rng = np.random.default_rng(seed)
+    x_vals = np.asarray(x_vals)
+    z_vals = np.asarray(z_vals)
+    if count <= 0 or len(x_vals) == 0 or len(z_vals) == 0:
+        return np.empty(0, np.int32), np.empty(0, np.int32)
+    a = x_vals[rng.integers(0, len(x_vals), count)].astype(np.int64)
+    b = z_vals[rng.integers(0, len(z_vals), count)].astype(np.int64)
+    miss = rng.random(count) < absent
+    side = rng.random(count) < 0.5
+    a[miss & side] = int(x_vals.max()) + 1 + rng.integers(0, 1000, int((miss & side).sum()))
+    b[miss & ~side] = int(z_vals.max()) + 1 + rng.integers(0, 1000, int((miss & ~side).sum()))
+    return (np.clip(a, -(1 << 31), (1 << 31) - 1).astype(np.int32),
+            np.clip(b, -(1 << 31), (1 << 31) - 1).astype(np.int32))
+
+
 # Named workloads with the paper-shaped sizes (Section 7.1 stand-ins).
 WORKLOADS = {
     # two-path, uniform, N = 20,000, fixed thresholds floor(sqrt(N)) = 141
