@@ -205,20 +205,30 @@ def random_small_relation(rng, n: int, dom_x: int, dom_y: int, offset_x: int = 0
 
 
 def candidate_pairs(x_vals: np.ndarray, z_vals: np.ndarray, count: int, seed: int = 0,
-                    absent: float = 0.0):
+                    absent: float = 0.0, x_weights=None, z_weights=None):
     """Candidate pairs (a, b) for a batch of boolean set intersection requests.
 
-    ``a`` is drawn uniformly from ``x_vals`` and ``b`` from ``z_vals`` (with
-    replacement, so pairs repeat); a fraction ``absent`` of the pairs names,
-    on one side, a value outside the given ones.
+    ``a`` is drawn from ``x_vals`` and ``b`` from ``z_vals`` (with
+    replacement, so pairs repeat), uniformly or with probability proportional
+    to the given weights (e.g. the values' degrees: large sets are asked about
+    more often); a fraction ``absent`` of the pairs names, on one side, a value
+    outside the given ones.
     """
     rng = np.random.default_rng(seed)
     x_vals = np.asarray(x_vals)
     z_vals = np.asarray(z_vals)
     if count <= 0 or len(x_vals) == 0 or len(z_vals) == 0:
         return np.empty(0, np.int32), np.empty(0, np.int32)
-    a = x_vals[rng.integers(0, len(x_vals), count)].astype(np.int64)
-    b = z_vals[rng.integers(0, len(z_vals), count)].astype(np.int64)
+
+    def draw(vals, w):
+        if w is None:
+            return vals[rng.integers(0, len(vals), count)].astype(np.int64)
+        cdf = np.cumsum(np.asarray(w, np.float64))
+        i = np.searchsorted(cdf, rng.random(count) * cdf[-1], side="right")
+        return vals[np.minimum(i, len(vals) - 1)].astype(np.int64)
+
+    a = draw(x_vals, x_weights)
+    b = draw(z_vals, z_weights)
     miss = rng.random(count) < absent
     side = rng.random(count) < 0.5
     a[miss & side] = int(x_vals.max()) + 1 + rng.integers(0, 1000, int((miss & side).sum()))

@@ -41,3 +41,22 @@ def test_star_relations_share_y_sequence():
     assert c > 0.8
     for x, y in rels:
         assert len(x) == 20_000 and _distinct(x, y) == 20_000
+
+
+def test_candidate_pairs_draws():
+    vals = np.array([-7, 3, 11, 40], np.int32)
+    a, b = W.candidate_pairs(vals, vals, 4000, seed=2)
+    assert set(a.tolist()) == set(vals.tolist()) and set(b.tolist()) == set(vals.tolist())
+    # weights: all mass on one value for x, proportional draws for z
+    a, b = W.candidate_pairs(vals, vals, 20000, seed=3, x_weights=[0, 0, 1, 0],
+                             z_weights=[1, 1, 2, 0])
+    assert (a == 11).all()
+    frac = np.array([(b == v).mean() for v in vals])
+    assert np.allclose(frac, [0.25, 0.25, 0.5, 0.0], atol=0.02)
+    # absent values lie outside the given ones, on one side of each such pair
+    a, b = W.candidate_pairs(vals, vals, 20000, seed=4, absent=0.3)
+    miss_a = ~np.isin(a, vals)
+    miss_b = ~np.isin(b, vals)
+    assert not (miss_a & miss_b).any()
+    assert abs((miss_a | miss_b).mean() - 0.3) < 0.02
+    assert len(W.candidate_pairs(vals, vals, 0)[0]) == 0
