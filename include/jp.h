@@ -185,6 +185,33 @@ int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t*
 int jp_two_path_filter(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, const jp_rel* T,
                        jp_result* out);
 
+/* Orders of jp_two_path_counts. */
+#define JP_ORDER_PAIRS  0    /* (x, z) ascending as signed int32 */
+#define JP_ORDER_COUNT  1    /* count descending; equal counts in (x, z) order */
+
+/* Set similarity join with witness counts (Section 1 "Set Similarity"; its ordered form,
+ * Section 4 "Ordered SSJ"): every pair (a, c) whose sets R(a, .) and S(c, .) share at least
+ * c_min values of y, with that number -- the entry M_ac of the product M1 x M2 of Section 2.2
+ * (c_min = 1 gives the two-path query with its counts).  The pairs a = c are included for a
+ * self-join, as the definition has them.  Algorithm 1's split is kept (the context's threshold
+ * mode): the heavy product's entries are read from the tensor cores' FP32 accumulators (exact
+ * below 2^24 shared values), the light witnesses are counted by sorting each x's light
+ * candidates, and the two counts of a pair are added.
+ *   S      NULL means S = R;
+ *   c_min  >= 1;
+ *   order  JP_ORDER_PAIRS or JP_ORDER_COUNT;
+ *   out    k = 3: col[0] = x, col[1] = z, col[2] = count (int32).
+ * Memory: the heavy count matrix (4 bytes per heavy x and heavy z pair; JP_EUNSUPPORTED above
+ * 64 GiB) and the light candidates of a range of x at a time (jp_set_count_chunk); one x with
+ * 2^31 or more light candidates, or 2^32 or more result pairs, gives JP_EUNSUPPORTED.  Other
+ * errors as jp_two_path. */
+int jp_two_path_counts(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int64_t c_min, int order,
+                       jp_result* out);
+
+/* Light candidates jp_two_path_counts sorts in one pass (default 2^27; a pass takes 40 bytes of
+ * workspace per candidate).  A smaller value bounds memory at the cost of more passes. */
+int jp_set_count_chunk(jp_ctx* ctx, int64_t candidates);
+
 /* Star query Q*_k (Section 2.1, Section 3.2) over rels[0..k-1], 2 <= k <= 8;
  * on success *out holds the sorted distinct k-tuples (k columns).  k = 2 is the two-path
  * query with S = rels[1]; k = 3 runs the Section 3.2 algorithm factorised on (x1, x2); for

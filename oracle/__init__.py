@@ -21,6 +21,10 @@ Contents:
   Section 3.3, Q_batch(x,z) = R(x,y), S(z,y), T(x,z), as the three-way join
   followed by the projection on (x, z) (numpy), and as a pure-Python loop over
   T for tiny inputs.
+* ``ssj`` / ``brute_ssj``: the set similarity join (Section 1) -- pairs whose
+  sets share at least c values, with the count -- in (x, z) order or by
+  decreasing count (Section 4, "Ordered SSJ"), from the C oracle's witness
+  counts, and as pure-Python set intersections for tiny inputs.
 * ``cost_model``: the threshold formulas (Section 3.1 closed forms, the
   Section 3.2 star cost, the Section 5 output estimate and Algorithm 3).
 """
@@ -40,7 +44,7 @@ _lock = threading.Lock()
 _lib = None
 
 __all__ = ["build", "two_path", "star", "two_path_row", "brute_two_path",
-           "brute_star", "normalise", "bsi", "brute_bsi"]
+           "brute_star", "normalise", "bsi", "brute_bsi", "ssj", "brute_ssj"]
 
 
 def build(force: bool = False) -> str:
@@ -259,4 +263,38 @@ def brute_bsi(rx, ry, tx, tz, sz=None, sy=None):
         yb = {y for z, y in S if z == b}
         if ya & yb:
             out.append((a, b))
+    return out
+
+
+def ssj(rx, ry, c_min: int = 1, sz=None, sy=None, order: str = "pairs"):
+    """(x, z, count) of the pairs whose sets share at least ``c_min`` y values.
+
+    ``order`` "pairs": (x, z) ascending; "count": count descending, equal
+    counts in (x, z) order.
+    """
+    ox, oz, oc = two_path(rx, ry, sz, sy, with_counts=True)
+    keep = oc >= c_min
+    ox, oz, oc = ox[keep], oz[keep], oc[keep]
+    if order == "count":
+        perm = np.lexsort((oz, ox, -oc.astype(np.int64)))
+        ox, oz, oc = ox[perm], oz[perm], oc[perm]
+    return ox, oz, oc
+
+
+def brute_ssj(rx, ry, c_min: int = 1, sz=None, sy=None):
+    """Pure-Python set intersections over every pair of sets: tiny inputs only."""
+    if sz is None:
+        sz, sy = rx, ry
+    A = {}
+    for a, b in zip(map(int, rx), map(int, ry)):
+        A.setdefault(a, set()).add(b)
+    B = {}
+    for c, b in zip(map(int, sz), map(int, sy)):
+        B.setdefault(c, set()).add(b)
+    out = []
+    for a in sorted(A):
+        for c in sorted(B):
+            k = len(A[a] & B[c])
+            if k >= c_min:
+                out.append((a, c, k))
     return out

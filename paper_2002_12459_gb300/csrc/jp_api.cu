@@ -22,6 +22,7 @@ struct jp_ctx {
     uint32_t* d_status = nullptr;      // device status word
     jp::Timer tm;
     jp_mlp* predictor = nullptr;       // borrowed model for JP_LEARNED
+    int64_t count_chunk = (int64_t)1 << 27;   // light candidates per pass of jp_two_path_counts
 };
 
 namespace jp {
@@ -428,6 +429,120 @@ int jp_two_path_filter(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, const jp_r
     if (!ctx) return JP_EINVAL;
     if (!T) return fail(ctx, JP_EINVAL, "T is NULL");
     return run_two_path(ctx, R, S, out, nullptr, T);
+}
+
+int jp_set_count_chunk(jp_ctx* ctx, int64_t candidates) {
+    if (!ctx) return JP_EINVAL;
+    if (candidates < 1) return fail(ctx, JP_EINVAL, "candidates must be >= 1");
+    ctx->count_chunk = candidates;
+    return JP_OK;
+}
+
+int jp_two_path_counts(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int64_t c_min, int order,
+                       jp_result* out) {
+    if (!ctx) return JP_EINVAL;
+    if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->k = 3;
+    if (c_min < 1) return fail(ctx, JP_EINVAL, "c_min must be >= 1");
+    if (order != JP_ORDER_PAIRS && order != JP_ORDER_COUNT) return fail(ctx, JP_EINVAL, "unknown order");
+    int rc = check_rel(ctx, R, "R");
+    if (rc) return rc;
+    if (S && (rc = check_rel(ctx, S, "S"))) return rc;
+    if (S && R->n + S->n >= ((int64_t)1 << 31)) return fail(ctx, JP_EUNSUPPORTED, "R and S together hold 2^31 or more tuples");
+    const auto t_start = std::chrono::steady_clock::now();
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = ctx->stream;
+        ctx->ws.begin();
+        const int64_t launches0 = jp::g_launches;
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
+        for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
+        ctx->tm.st = st;
+        jp::g_timer = &ctx->tm;
+        ctx->tm.begin(jp::TM_TOTAL);
+        const jp_rel Rd = to_device(ctx, R);
+        jp_rel Sd;
+        if (S) Sd = to_device(ctx, S);
+        const bool self = (S == nullptr) || (S->x == R->x && S->y == R->y && S->n == R->n);
+        jp::Graph g;
+        ctx->tm.begin(jp::TM_BUILD);
+        jp::build_graph(&Rd, self ? nullptr : &Sd, g, ctx->ws, st, ctx->d_status, ctx->hist_host,
+                        ctx->host_scalars);
+        ctx->tm.end(jp::TM_BUILD);
+        jp::Partition p;
+        double out_est = 0;
+        int judged = 0;
+        ctx->tm.begin(jp::TM_SELECT);
+        jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
+                              ctx->predictor, &judged);
+        ctx->tm.end(jp::TM_SELECT);
+        ctx->tm.begin(jp::TM_PARTITION);
+        jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
+        ctx->tm.end(jp::TM_PARTITION);
+        jp::Heavy h;
+        ctx->tm.begin(jp::TM_PACK);
+        jp::heavy_pack(g, p, h, ctx->ws, st);
+        ctx->tm.end(jp::TM_PACK);
+        jp::CountResult cr;
+        jp::count_pairs(g, p, h, c_min, order, cr, ctx->ws, st, ctx->d_status, ctx->hist_host,
+                        ctx->count_chunk);
+        status_check(ctx);
+        if (cr.n > 0) {
+            const size_t col = ((size_t)cr.n * sizeof(int32_t) + 255) & ~(size_t)255;
+            block_bytes = 3 * col + 256;
+            block = ctx->ws.raw_alloc(block_bytes);
+            if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
+            const int32_t* src[3] = {cr.x, cr.z, cr.cnt};
+            for (int i = 0; i < 3; ++i) {
+                out->col[i] = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(block) + i * col);
+                JP_CUDA_TRY(cudaMemcpyAsync(out->col[i], src[i], (size_t)cr.n * sizeof(int32_t),
+                                            cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        ctx->tm.end(jp::TM_TOTAL);
+        status_check(ctx);
+        jp::g_timer = nullptr;
+        out->count = cr.n;
+        out->_block = block;
+        out->_bytes = block_bytes;
+        jp_stats& s = ctx->stats;
+        std::memset(&s, 0, sizeof(s));
+        s.n_r = g.nr;
+        s.n_s = g.ns;
+        s.dom_x = g.nx;
+        s.dom_y = g.ny;
+        s.dom_z = g.nz;
+        s.out_join = g.out_join;
+        s.out_estimate = out_est;
+        s.delta1 = p.d1;
+        s.delta2 = p.d2;
+        s.threshold_mode = ctx->mode;
+        s.u = p.u;
+        s.v = p.v;
+        s.w = p.w;
+        s.light_candidates = cr.candidates;
+        s.out_count = cr.n;
+        s.learned_judged = judged;
+        s.kernel_launches = jp::g_launches - launches0;
+        for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
+        s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        ctx->have_stats = true;
+        ctx->err.clear();
+        return JP_OK;
+    } catch (const jp::Error& e) {
+        jp::g_timer = nullptr;
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, e.code, e.msg);
+    } catch (const std::bad_alloc&) {
+        jp::g_timer = nullptr;
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, JP_ENOMEM, "host allocation failed");
+    }
 }
 
 int jp_measure_peaks(jp_ctx* ctx, double* fp8_tflops, double* int8_mma_sync_tflops) {

@@ -1,0 +1,449 @@
+// Witness counts of the two-path query and the set similarity join.
+//
+// For a pair (a, c) the number of y with R(a, y) and S(c, y) is the entry
+// M_ac of the product M1 x M2 (Section 2.2).  The set similarity join
+// (Section 1, "Set Similarity") keeps the pairs with M_ac >= c_min; its
+// ordered form (Section 4, "Ordered SSJ") lists them by decreasing M_ac.
+//
+// Algorithm 1's split divides the witnesses disjointly: (a, y, c) is in the
+// heavy product iff a, y and c are all heavy (both tuples in R+ and S+);
+// otherwise it is one light candidate of a -- taken from S[y] when (a, y) is
+// light, from the light z of S[y] when (a, y) is heavy.  Hence
+// M_ac = P_ac + L_ac, P the heavy product's entry (0 off the heavy block) and
+// L_ac the multiplicity of c among a's light candidates.
+//
+// x ids are processed in ranges whose candidates fit a budget.  A range's
+// candidates are written as keys (x - x0, z id), sorted and run-length
+// counted; its rows of P are compacted to the same keys (already in order)
+// and merged in, equal keys summed; pairs counted at least c_min are written
+// out.  Ranges follow each other in x order, so their concatenation is in
+// (x, z) order.
+#include <algorithm>
+#include <vector>
+
+#include "jp_internal.cuh"
+
+namespace jp {
+namespace {
+
+inline int G(int64_t n) { return grid_for(n, 256, 152 * 16); }
+inline int GW(int64_t n) { return grid_for(n * 32, 256, 152 * 16); }   // a warp per item
+
+// candidates of x: sum over its y of |S[y]|, or of |light z of S[y]| when (x, y) is heavy
+__global__ void cand_count_kernel(const int32_t* __restrict__ rxoff, const int32_t* __restrict__ rycol,
+                                  int64_t nx, const int32_t* __restrict__ hx,
+                                  const int32_t* __restrict__ hy, const int32_t* __restrict__ syoff,
+                                  const int32_t* __restrict__ sloff, int64_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nx; x += nw) {
+        const bool ah = hx[x] >= 0;
+        int64_t s = 0;
+        for (int32_t k = rxoff[x] + lane; k < rxoff[x + 1]; k += 32) {
+            const int32_t b = rycol[k];
+            const int32_t j = ah ? hy[b] : -1;
+            s += (j >= 0) ? (sloff[j + 1] - sloff[j]) : (syoff[b + 1] - syoff[b]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) cnt[x] = s;
+    }
+}
+
+// the candidates of x in [x0, x1) as keys (x - x0) << 32 | z, at coff[x] - coff[x0]
+__global__ void cand_fill_kernel(int64_t x0, int64_t x1, const int64_t* __restrict__ coff,
+                                 const int32_t* __restrict__ rxoff, const int32_t* __restrict__ rycol,
+                                 const int32_t* __restrict__ hx, const int32_t* __restrict__ hy,
+                                 const int32_t* __restrict__ syoff, const int32_t* __restrict__ szcol,
+                                 const int32_t* __restrict__ sloff, const int32_t* __restrict__ slcol,
+                                 uint64_t* __restrict__ keys) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t c0 = coff[x0];
+    for (int64_t x = x0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < x1; x += nw) {
+        int64_t base = coff[x] - c0;
+        const bool ah = hx[x] >= 0;
+        const uint64_t hi = (uint64_t)(x - x0) << 32;
+        for (int32_t k = rxoff[x]; k < rxoff[x + 1]; ++k) {
+            const int32_t b = rycol[k];
+            const int32_t j = ah ? hy[b] : -1;
+            const int32_t* list;
+            int32_t len;
+            if (j >= 0) {
+                list = slcol + sloff[j];
+                len = sloff[j + 1] - sloff[j];
+            } else {
+                list = szcol + syoff[b];
+                len = syoff[b + 1] - syoff[b];
+            }
+            for (int32_t e = lane; e < len; e += 32) keys[base + e] = hi | (uint32_t)list[e];
+            base += len;
+        }
+    }
+}
+
+__global__ void run_mark_kernel(const uint64_t* __restrict__ k, int64_t n, uint32_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
+}
+
+__global__ void run_start_kernel(const uint64_t* __restrict__ k, int64_t n,
+                                 const uint32_t* __restrict__ flag, const uint32_t* __restrict__ idx,
+                                 uint64_t* __restrict__ uk, uint32_t* __restrict__ start) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) {
+            uk[idx[i]] = k[i];
+            start[idx[i]] = (uint32_t)i;
+        }
+}
+
+__global__ void run_length_kernel(const uint32_t* __restrict__ start, int64_t m, int64_t n,
+                                  uint32_t* __restrict__ cnt) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x)
+        cnt[j] = (j + 1 < m ? start[j + 1] : (uint32_t)n) - start[j];
+}
+
+// nonzero entries of the heavy rows [h0, h1) of the count matrix; a warp per row
+__global__ void heavy_nnz_kernel(const uint32_t* __restrict__ C, int64_t ldc, int64_t h0, int64_t h1,
+                                 int64_t w, uint32_t* __restrict__ nnz) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = h0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); h < h1; h += nw) {
+        const uint32_t* row = C + h * ldc;
+        uint32_t s = 0;
+        for (int64_t j = lane; j < w; j += 32) s += row[j] != 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) nnz[h - h0] = s;
+    }
+}
+
+__global__ void heavy_keys_kernel(const uint32_t* __restrict__ C, int64_t ldc, int64_t h0, int64_t h1,
+                                  int64_t w, const int32_t* __restrict__ hx_inv,
+                                  const int32_t* __restrict__ hz_inv, int64_t x0,
+                                  const uint32_t* __restrict__ off, uint64_t* __restrict__ keys,
+                                  uint32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = h0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); h < h1; h += nw) {
+        const uint32_t* row = C + h * ldc;
+        const uint64_t hi = (uint64_t)(hx_inv[h] - x0) << 32;
+        uint32_t base = off[h - h0];
+        for (int64_t j0 = 0; j0 < w; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const uint32_t v = j < w ? row[j] : 0u;
+            const unsigned m = __ballot_sync(0xffffffffu, v != 0u);
+            if (v != 0u) {
+                const uint32_t p = base + __popc(m & ((1u << lane) - 1u));
+                keys[p] = hi | (uint32_t)hz_inv[j];
+                cnt[p] = v;
+            }
+            base += __popc(m);
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n, uint64_t k) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// heavy pairs already among the light pairs add their count there; the rest are flagged
+__global__ void merge_probe_kernel(const uint64_t* __restrict__ hk, const uint32_t* __restrict__ hc,
+                                   int64_t nh, const uint64_t* __restrict__ lk, uint32_t* lc,
+                                   int64_t nl, uint32_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nh;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = lower_bound_u64(lk, nl, hk[i]);
+        if (p < nl && lk[p] == hk[i]) {
+            lc[p] += hc[i];          // keys are distinct within each list: one writer per p
+            flag[i] = 0u;
+        } else {
+            flag[i] = 1u;
+        }
+    }
+}
+
+__global__ void compact_kv_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c,
+                                  int64_t n, const uint32_t* __restrict__ flag,
+                                  const uint32_t* __restrict__ pos, uint64_t* __restrict__ ok,
+                                  uint32_t* __restrict__ oc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) {
+            ok[pos[i]] = k[i];
+            oc[pos[i]] = c[i];
+        }
+}
+
+// merge of two sorted lists with no key in common: element i of a goes to
+// i + (number of b keys below it)
+__global__ void merge_place_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ac,
+                                   int64_t na, const uint64_t* __restrict__ bk, int64_t nb,
+                                   uint64_t* __restrict__ ok, uint32_t* __restrict__ oc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = i + lower_bound_u64(bk, nb, ak[i]);
+        ok[p] = ak[i];
+        oc[p] = ac[i];
+    }
+}
+
+__global__ void keep_flag_kernel(const uint32_t* __restrict__ c, int64_t n, uint32_t c_min,
+                                 uint32_t* __restrict__ flag) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = c[i] >= c_min ? 1u : 0u;
+}
+
+__global__ void write_pairs_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c,
+                                   int64_t n, const uint32_t* __restrict__ flag,
+                                   const uint32_t* __restrict__ pos, int64_t x0,
+                                   const int32_t* __restrict__ xval, const int32_t* __restrict__ zval,
+                                   int32_t* __restrict__ ox, int32_t* __restrict__ oz,
+                                   int32_t* __restrict__ oc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) {
+            const uint32_t p = pos[i];
+            ox[p] = xval[x0 + (int64_t)(k[i] >> 32)];
+            oz[p] = zval[(uint32_t)k[i]];
+            oc[p] = (int32_t)c[i];
+        }
+}
+
+// sort keys for decreasing count, ties in position order: (~count) << 32 | position
+__global__ void count_order_keys_kernel(const int32_t* __restrict__ c, int64_t n,
+                                        uint64_t* __restrict__ k) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        k[i] = ((uint64_t)(~(uint32_t)c[i]) << 32) | (uint32_t)i;
+}
+
+__global__ void gather3_kernel(const uint64_t* __restrict__ k, int64_t n, const int32_t* __restrict__ x,
+                               const int32_t* __restrict__ z, const int32_t* __restrict__ c,
+                               int32_t* __restrict__ ox, int32_t* __restrict__ oz,
+                               int32_t* __restrict__ oc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = (uint32_t)k[i];
+        ox[i] = x[j];
+        oz[i] = z[j];
+        oc[i] = c[j];
+    }
+}
+
+template <class T> T read1(const T* d, cudaStream_t st) {
+    T v{};
+    JP_CUDA_TRY(cudaMemcpyAsync(&v, d, sizeof(T), cudaMemcpyDeviceToHost, st));
+    JP_CUDA_TRY(cudaStreamSynchronize(st));
+    return v;
+}
+
+// Scratch that grows on demand (the arena never frees within a query).
+template <class T> struct Grow {
+    T* p = nullptr;
+    int64_t cap = -1;
+    T* need(int64_t n, Arena& ws) {
+        if (n > cap) {
+            cap = std::max<int64_t>(n, 1);
+            p = ws.get<T>((size_t)cap);
+        }
+        return p;
+    }
+};
+
+}  // namespace
+
+void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_min, int order,
+                 CountResult& out, Arena& ws, cudaStream_t st, uint32_t* d_status,
+                 uint32_t* hist_host, int64_t chunk_candidates) {
+    out = CountResult{};
+    const int64_t nx = g.nx;
+    if (nx == 0) return;
+    if (c_min < 1) c_min = 1;
+    const uint32_t cmin = c_min > 0x7fffffff ? 0x7fffffffu : (uint32_t)c_min;
+
+    // heavy product entries
+    uint32_t* C = nullptr;
+    if (h.present) {
+        const size_t bytes = (size_t)h.u_pad * (size_t)h.w_pad * sizeof(uint32_t);
+        if (bytes > ((size_t)1 << 36))
+            throw Error{JP_EUNSUPPORTED, "the heavy count matrix would exceed 64 GiB"};
+        C = ws.get<uint32_t>((size_t)h.u_pad * (size_t)h.w_pad);
+        heavy_gemm_counts(h, C, d_status, st);
+    }
+
+    // light candidates per x and their offsets
+    int64_t* cnt = ws.get<int64_t>(nx + 1);
+    int64_t* coff = ws.get<int64_t>(nx + 1);
+    cand_count_kernel<<<GW(nx), 256, 0, st>>>(g.rxoff, g.rycol, nx, p.hx, p.hy, g.syoff, p.sloff, cnt);
+    JP_CHECK_LAUNCH();
+    scan_i64(cnt, coff, nx, coff + nx, ws, st);
+    std::vector<int64_t> hoff_host((size_t)nx + 1);
+    JP_CUDA_TRY(cudaMemcpyAsync(hoff_host.data(), coff, (nx + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> hx_inv_host((size_t)p.u);
+    if (p.u > 0)
+        JP_CUDA_TRY(cudaMemcpyAsync(hx_inv_host.data(), p.hx_inv, p.u * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st));
+    JP_CUDA_TRY(cudaStreamSynchronize(st));
+    out.candidates = hoff_host[nx];
+    int64_t max_row = 0;
+    for (int64_t x = 0; x < nx; ++x) max_row = std::max(max_row, hoff_host[x + 1] - hoff_host[x]);
+    if (max_row >= ((int64_t)1 << 31))
+        throw Error{JP_EUNSUPPORTED, "one x has 2^31 or more light candidates"};
+    const int64_t cap = std::max<int64_t>(
+        std::max<int64_t>(std::min<int64_t>(chunk_candidates, out.candidates), 1), max_row);
+
+    uint64_t* keys = ws.get<uint64_t>(cap);
+    uint64_t* tmp = ws.get<uint64_t>(cap);
+    uint32_t* flag = ws.get<uint32_t>(cap);
+    uint32_t* idx = ws.get<uint32_t>(cap);
+    uint64_t* uk = ws.get<uint64_t>(cap);
+    uint32_t* start = ws.get<uint32_t>(cap);
+    uint32_t* lc = ws.get<uint32_t>(cap);
+    uint32_t* d_total = ws.get<uint32_t>(1);
+    Grow<uint32_t> hnnz, hoffs, hflag, hpos, hc, h2c, mc, kflag, kpos;
+    Grow<uint64_t> hk, h2k, mk;
+
+    struct Piece { int32_t* x; int32_t* z; int32_t* c; int64_t n; };
+    std::vector<Piece> pieces;
+    int64_t total = 0;
+    for (int64_t x0 = 0; x0 < nx;) {
+        // the longest range of x from x0 whose candidates fit the scratch
+        int64_t x1 = std::upper_bound(hoff_host.begin() + x0 + 1, hoff_host.end(),
+                                      hoff_host[x0] + cap) - hoff_host.begin() - 1;
+        if (x1 <= x0) x1 = x0 + 1;
+        const int64_t nc = hoff_host[x1] - hoff_host[x0];
+        // light pairs of the range: sorted keys, run lengths
+        int64_t m = 0;
+        if (nc > 0) {
+            cand_fill_kernel<<<GW(x1 - x0), 256, 0, st>>>(x0, x1, coff, g.rxoff, g.rycol, p.hx, p.hy,
+                                                          g.syoff, g.szcol, p.sloff, p.slcol, keys);
+            JP_CHECK_LAUNCH();
+            uint64_t* s = radix_sort_u64(keys, tmp, nc, ws, st, hist_host);
+            run_mark_kernel<<<G(nc), 256, 0, st>>>(s, nc, flag);
+            JP_CHECK_LAUNCH();
+            scan_u32(flag, idx, nc, d_total, ws, st);
+            run_start_kernel<<<G(nc), 256, 0, st>>>(s, nc, flag, idx, uk, start);
+            JP_CHECK_LAUNCH();
+            m = read1(d_total, st);
+            run_length_kernel<<<G(m), 256, 0, st>>>(start, m, nc, lc);
+            JP_CHECK_LAUNCH();
+        }
+        // heavy pairs of the range: rows h0..h1 of the count matrix
+        const int64_t h0 = std::lower_bound(hx_inv_host.begin(), hx_inv_host.end(), (int32_t)x0) -
+                           hx_inv_host.begin();
+        const int64_t h1 = std::lower_bound(hx_inv_host.begin(), hx_inv_host.end(),
+                                            (int32_t)std::min<int64_t>(x1, 0x7fffffff)) -
+                           hx_inv_host.begin();
+        int64_t nh = 0;
+        if (C && h1 > h0) {
+            uint32_t* nnz = hnnz.need(h1 - h0, ws);
+            uint32_t* off = hoffs.need(h1 - h0, ws);
+            heavy_nnz_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, nnz);
+            JP_CHECK_LAUNCH();
+            scan_u32(nnz, off, h1 - h0, d_total, ws, st);
+            nh = read1(d_total, st);
+            if (nh > 0) {
+                heavy_keys_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, p.hx_inv,
+                                                               p.hz_inv, x0, off, hk.need(nh, ws),
+                                                               hc.need(nh, ws));
+                JP_CHECK_LAUNCH();
+            }
+        }
+        // merge: equal keys summed into the light list, the others placed between
+        const uint64_t* fk = uk;
+        const uint32_t* fc = lc;
+        int64_t nf = m;
+        if (nh > 0) {
+            uint32_t* hf = hflag.need(nh, ws);
+            uint32_t* hp = hpos.need(nh, ws);
+            if (m > 0) {
+                merge_probe_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, uk, lc, m, hf);
+                JP_CHECK_LAUNCH();
+            } else {
+                keep_flag_kernel<<<G(nh), 256, 0, st>>>(hc.p, nh, 1u, hf);   // every entry is >= 1
+                JP_CHECK_LAUNCH();
+            }
+            scan_u32(hf, hp, nh, d_total, ws, st);
+            const int64_t nh2 = read1(d_total, st);
+            if (nh2 > 0) {
+                uint64_t* k2 = h2k.need(nh2, ws);
+                uint32_t* c2 = h2c.need(nh2, ws);
+                compact_kv_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, hf, hp, k2, c2);
+                JP_CHECK_LAUNCH();
+                uint64_t* ok = mk.need(m + nh2, ws);
+                uint32_t* oc = mc.need(m + nh2, ws);
+                if (m > 0) {
+                    merge_place_kernel<<<G(m), 256, 0, st>>>(uk, lc, m, k2, nh2, ok, oc);
+                    JP_CHECK_LAUNCH();
+                }
+                merge_place_kernel<<<G(nh2), 256, 0, st>>>(k2, c2, nh2, uk, m, ok, oc);
+                JP_CHECK_LAUNCH();
+                fk = ok;
+                fc = oc;
+                nf = m + nh2;
+            }
+        }
+        // pairs counted at least c_min
+        if (nf > 0) {
+            uint32_t* kf = kflag.need(nf, ws);
+            uint32_t* kp = kpos.need(nf, ws);
+            keep_flag_kernel<<<G(nf), 256, 0, st>>>(fc, nf, cmin, kf);
+            JP_CHECK_LAUNCH();
+            scan_u32(kf, kp, nf, d_total, ws, st);
+            const int64_t nk = read1(d_total, st);
+            if (nk > 0) {
+                Piece pc{ws.get<int32_t>(nk), ws.get<int32_t>(nk), ws.get<int32_t>(nk), nk};
+                write_pairs_kernel<<<G(nf), 256, 0, st>>>(fk, fc, nf, kf, kp, x0, g.xval, g.zval,
+                                                          pc.x, pc.z, pc.c);
+                JP_CHECK_LAUNCH();
+                pieces.push_back(pc);
+                total += nk;
+            }
+        }
+        x0 = x1;
+    }
+    if (total >= ((int64_t)1 << 32)) throw Error{JP_EUNSUPPORTED, "2^32 or more result pairs"};
+    // the pieces one after another
+    int32_t* X = ws.get<int32_t>(total + 1);
+    int32_t* Z = ws.get<int32_t>(total + 1);
+    int32_t* K = ws.get<int32_t>(total + 1);
+    int64_t at = 0;
+    for (const Piece& pc : pieces) {
+        JP_CUDA_TRY(cudaMemcpyAsync(X + at, pc.x, pc.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        JP_CUDA_TRY(cudaMemcpyAsync(Z + at, pc.z, pc.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        JP_CUDA_TRY(cudaMemcpyAsync(K + at, pc.c, pc.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        at += pc.n;
+    }
+    if (order == 1 && total > 1) {
+        uint64_t* ok0 = ws.get<uint64_t>(total);
+        uint64_t* ok1 = ws.get<uint64_t>(total);
+        count_order_keys_kernel<<<G(total), 256, 0, st>>>(K, total, ok0);
+        JP_CHECK_LAUNCH();
+        uint64_t* s = radix_sort_u64(ok0, ok1, total, ws, st, hist_host);
+        int32_t* X2 = ws.get<int32_t>(total);
+        int32_t* Z2 = ws.get<int32_t>(total);
+        int32_t* K2 = ws.get<int32_t>(total);
+        gather3_kernel<<<G(total), 256, 0, st>>>(s, total, X, Z, K, X2, Z2, K2);
+        JP_CHECK_LAUNCH();
+        X = X2;
+        Z = Z2;
+        K = K2;
+    }
+    out.x = X;
+    out.z = Z;
+    out.cnt = K;
+    out.n = total;
+}
+
+}  // namespace jp

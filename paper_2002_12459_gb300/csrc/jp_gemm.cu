@@ -164,6 +164,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 // One 128 x 256 output tile per CTA.  K is consumed in BK-byte stages through
 // a STAGES-deep TMA ring; each stage feeds BK/32 MMAs (K = 32 per FP8 MMA).
+// The epilogue writes one bit per entry (M_ac > 0) into G, or with COUNTS the
+// entries themselves (the witness counts, exact below 2^24) as uint32 into G
+// read as a count matrix of g_stride entries per row.
+template <bool COUNTS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     heavy_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, int num_kb, uint32_t* __restrict__ G,
@@ -205,9 +209,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     if (kb0 >= kb1) {
         if (threadIdx.x >= 64) {               // warps 2-5: one row each thread
-            uint32_t* grow = G + (int64_t)(m0 + (int)threadIdx.x - 64) * g_stride + (n0 >> 5);
+            if constexpr (COUNTS) {
+                uint4* crow = reinterpret_cast<uint4*>(
+                    G + (int64_t)(m0 + (int)threadIdx.x - 64) * g_stride + n0);
+                for (int j = 0; j < BN / 4; ++j) crow[j] = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                uint32_t* grow = G + (int64_t)(m0 + (int)threadIdx.x - 64) * g_stride + (n0 >> 5);
 #pragma unroll
-            for (int j = 0; j < BN / 32; ++j) grow[j] = 0u;
+                for (int j = 0; j < BN / 32; ++j) grow[j] = 0u;
+            }
         }
         return;
     }
@@ -276,15 +286,29 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const int row = m0 + q * 32 + lane;
         if (mbar_wait(accum, 0, status)) {
             tc_fence_after();
-            uint32_t* grow = G + (int64_t)row * g_stride + (n0 >> 5);
+            if constexpr (COUNTS) {
+                uint4* crow = reinterpret_cast<uint4*>(G + (int64_t)row * g_stride + n0);
 #pragma unroll 1
-            for (int j = 0; j < BN / 32; ++j) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
-                uint32_t bits = 0;
+                for (int j = 0; j < BN / 32; ++j) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) bits |= (r[i] != 0u ? 1u : 0u) << i;
-                grow[j] = bits;
+                    for (int i = 0; i < 32; i += 4)
+                        crow[j * 8 + i / 4] = make_uint4(
+                            (uint32_t)__uint_as_float(r[i]), (uint32_t)__uint_as_float(r[i + 1]),
+                            (uint32_t)__uint_as_float(r[i + 2]), (uint32_t)__uint_as_float(r[i + 3]));
+                }
+            } else {
+                uint32_t* grow = G + (int64_t)row * g_stride + (n0 >> 5);
+#pragma unroll 1
+                for (int j = 0; j < BN / 32; ++j) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
+                    uint32_t bits = 0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) bits |= (r[i] != 0u ? 1u : 0u) << i;
+                    grow[j] = bits;
+                }
             }
         }
     }
@@ -573,15 +597,34 @@ void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t s
     CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
     static bool attr = false;
     if (!attr) {
-        JP_CUDA_TRY(cudaFuncSetAttribute(heavy_gemm_kernel,
+        JP_CUDA_TRY(cudaFuncSetAttribute(heavy_gemm_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)GEMM_SMEM));
         attr = true;
     }
     const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
     tbegin(TM_GEMM);
-    heavy_gemm_kernel<<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
+    heavy_gemm_kernel<false><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
         ma, mb, (int)(h.v_pad / BK), h.G, h.g_stride, d_status, tiles, gx, gy);
+    JP_CHECK_LAUNCH();
+    tend(TM_GEMM);
+}
+
+void heavy_gemm_counts(const Heavy& h, uint32_t* C, uint32_t* d_status, cudaStream_t st) {
+    if (!h.present) return;
+    CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
+    CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
+    static bool attr = false;
+    if (!attr) {
+        JP_CUDA_TRY(cudaFuncSetAttribute(heavy_gemm_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GEMM_SMEM));
+        attr = true;
+    }
+    const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
+    tbegin(TM_GEMM);
+    heavy_gemm_kernel<true><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
+        ma, mb, (int)(h.v_pad / BK), C, h.w_pad, d_status, nullptr, gx, gy);
     JP_CHECK_LAUNCH();
     tend(TM_GEMM);
 }

@@ -208,6 +208,22 @@ void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStr
 // tiles: null, or (batches) the K-block range of every tile (batch_tile_ranges).
 void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
                 const int2* tiles = nullptr);
+// The heavy product's entries (witness counts) as uint32 into C[u_pad][w_pad].
+void heavy_gemm_counts(const Heavy& h, uint32_t* C, uint32_t* d_status, cudaStream_t st);
+
+// Witness counts and the set similarity join (jp_counts.cu): the pairs with
+// M_ac >= c_min as (x, z, count) columns in the workspace, in (x, z) order or
+// by decreasing count.  Returns the number of pairs and the light candidates.
+struct CountResult {
+    int32_t* x = nullptr;
+    int32_t* z = nullptr;
+    int32_t* cnt = nullptr;
+    int64_t n = 0;
+    int64_t candidates = 0;
+};
+void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_min, int order,
+                 CountResult& out, Arena& ws, cudaStream_t st, uint32_t* d_status,
+                 uint32_t* hist_host, int64_t chunk_candidates);
 
 // Light part + union (jp_light.cu)
 // A row's list: tmp_off >= 0 is its offset in tmp, holding z values, or, with

@@ -95,6 +95,11 @@ def load(path: str = LIB_PATH):
             lib.jp_two_path_filter.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
                                                ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
             lib.jp_two_path_filter.restype = i32
+            lib.jp_two_path_counts.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
+                                               i64, i32, ctypes.POINTER(jp_result)]
+            lib.jp_two_path_counts.restype = i32
+            lib.jp_set_count_chunk.argtypes = [vp, i64]
+            lib.jp_set_count_chunk.restype = i32
             lib.jp_selftest_wait.argtypes = [vp, i64]
             lib.jp_selftest_wait.restype = i32
             dp = ctypes.POINTER(ctypes.c_double)
@@ -219,6 +224,26 @@ class Context:
                                              ctypes.byref(res))
         self._check(rc)
         return self._take(res)
+
+    def two_path_counts(self, rx, ry, sz=None, sy=None, c_min: int = 1, order: str = "pairs"):
+        """Pairs (a, c) sharing at least c_min y, with the count: (x, z, count) columns.
+
+        ``order`` is "pairs" ((x, z) ascending) or "count" (count descending, ties in
+        (x, z) order).
+        """
+        R = _rel_of(rx, ry)
+        S = _rel_of(sz, sy) if sz is not None else None
+        o = {"pairs": 0, "count": 1}[order]
+        res = jp_result()
+        with self._torch.cuda.stream(self.stream):
+            rc = self.lib.jp_two_path_counts(self.h, ctypes.byref(R),
+                                             ctypes.byref(S) if S else None, int(c_min), o,
+                                             ctypes.byref(res))
+        self._check(rc)
+        return self._take(res)
+
+    def set_count_chunk(self, candidates: int):
+        self._check(self.lib.jp_set_count_chunk(self.h, int(candidates)))
 
     def measure_peaks(self) -> dict:
         """Measured dense tensor rates (TFLOP/s): tcgen05 FP8 and INT8 mma.sync."""
