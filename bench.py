@@ -503,6 +503,141 @@ def run_star(args):
     }
 
 
+# ----------------------------------------------------------------- set similarity join
+def ssj_rooflines(st, peaks, ms, cand, distinct_light):
+    """Phases of jp_two_path_counts against their rooflines (algorithmic work per step).
+
+    counting product: 2 u v w flops; candidate fill: per candidate an id read (4 B) and a key
+    written (8 B); sort and run lengths: per candidate the key read once (8 B), per distinct light
+    pair a key and a count written (12 B); heavy rows, merge and output: per output pair 12 B
+    written, per distinct pair 12 B read.
+    """
+    hbm = peaks["hbm_gbs"]
+    out = st["out_count"]
+    res = {}
+    if ms.get(4, 0) > 0 and st["u"] > 0:
+        f8 = peaks.get("fp8_tcgen05_tflops") or 2.0 * peaks["bf16_tflops"]
+        ach = 2.0 * st["u"] * st["v"] * st["w"] / (ms[4] * 1e-3) / 1e12
+        res["heavy_gemm_kernel<true>"] = {"ms": ms[4], "bound": "tensor", "achieved": ach,
+                                          "peak": f8, "unit": "TFLOP/s", "frac": ach / f8,
+                                          "traffic": None}
+    work = {13: ("cand_fill_kernel", 12.0 * cand),
+            14: ("radix sort + run lengths", 8.0 * cand + 12.0 * distinct_light),
+            15: ("heavy rows, merge, output", 12.0 * out + 12.0 * distinct_light)}
+    for slot, (name, byts) in work.items():
+        if ms.get(slot, 0) > 0:
+            ach = byts / (ms[slot] * 1e-3) / 1e9
+            res[name] = {"ms": ms[slot], "bound": "hbm", "achieved": ach, "peak": hbm,
+                         "unit": "GB/s", "frac": ach / hbm, "traffic": None}
+    top = max(res, key=lambda k: res[k]["ms"])
+    return dict(res[top], kernel=top), res
+
+
+def run_ssj(args):
+    """Ordered set similarity join (pairs sharing >= c_min y, by decreasing count)."""
+    import torch
+    from paper_2002_12459_gb300 import build, jp
+    from paper_2002_12459_gb300 import workloads as W
+
+    build.build()
+    wl = W.WORKLOADS[args.workload]
+    c_min = wl["c_min"]
+    t = time.time()
+    rx, ry = W.make(args.workload)
+    log(f"[bench] workload {args.workload}: {len(rx)} tuples in {time.time() - t:.1f}s")
+    dx, dy = torch.from_numpy(rx).cuda(), torch.from_numpy(ry).cuda()
+    ctx = jp.Context(0)
+    tensor_peaks = ctx.measure_peaks()
+    ctx.set_threshold(args.mode, args.delta1, args.delta2)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for i in range(args.warmup):
+        cols = ctx.two_path_counts(dx, dy, c_min=c_min, order="count")
+        del cols
+        torch.cuda.synchronize()
+        log(f"[bench] warmup {i}: {ctx.stats()['ms_pass'][12]:.2f} ms")
+    sampler = ClockSampler(0)
+    sampler.start()
+    step_ms, slot_ms, st = [], {}, None
+    cols = None
+    for i in range(args.steps):
+        cols = None
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
+        cols = ctx.two_path_counts(dx, dy, c_min=c_min, order="count")
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = ctx.stats()
+        step_ms.append(ms)
+        for k, v in enumerate(st["ms_pass"]):
+            slot_ms[k] = slot_ms.get(k, 0.0) + v / args.steps
+        log(f"[bench] step {i}: {ms:.2f} ms, OUT={st['out_count']}, ranges={st['count_ranges']}, "
+            f"launches={st['kernel_launches']}")
+    clocks = sampler.stop()
+    mean_ms = sum(step_ms) / len(step_ms)
+    out = st["out_count"]
+
+    # sampled bit-exact check: the pairs of an x range (taken out of the count order and
+    # sorted by (x, z) on the device) against the oracle's counts
+    import oracle
+    oracle.build()
+    ox, oz, oc = cols
+    vals, cnts = np.unique(rx, return_counts=True)
+    hub = int(vals[np.argmax(cnts)])
+    checked, ok = 0, True
+    for lo, hi in [(hub, hub), (int(vals[len(vals) // 2]), int(vals[len(vals) // 2 + 300]))]:
+        sel = (ox >= lo) & (ox <= hi)
+        gx, gz, gc = ox[sel].long(), oz[sel].long(), oc[sel]
+        perm = torch.argsort(gx * (1 << 32) + (gz + (1 << 31)))
+        wx, wz, wc = oracle.two_path(rx, ry, x_lo=lo, x_hi=hi, with_counts=True)
+        keep = wc >= c_min
+        ok &= (np.array_equal(gx[perm].cpu().numpy(), wx[keep])
+               and np.array_equal(gz[perm].cpu().numpy(), wz[keep])
+               and np.array_equal(gc[perm].cpu().numpy(), wc[keep]))
+        checked += int(keep.sum())
+    ok &= bool((oc[1:] <= oc[:-1]).all())
+    parity = {"x_ranges": "the largest-degree x, and 301 x values mid-domain", "pairs_checked": checked,
+              "count_order_nonincreasing": bool((oc[1:] <= oc[:-1]).all()), "bit_exact": bool(ok)}
+    del cols, ox, oz, oc, sel, gx, gz, gc
+
+    base = None
+    if not args.no_cpu:
+        lo, hi, k, c, nx, ctot = cpu_sample(rx, ry, 1.0e7)
+        t = time.perf_counter()
+        wx, wz, wc = oracle.two_path(rx, ry, x_lo=lo, x_hi=hi, with_counts=True)
+        n = int((wc >= c_min).sum())
+        secs = time.perf_counter() - t
+        base = {"value": n / secs, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                "sample": (f"x values {lo}..{hi} ({k} of {nx} x values, {c:.3g} of {ctot:.3g} join "
+                           f"candidates), single-threaded C oracle with witness counts, filtered "
+                           f">= {c_min}; {n} pairs in {secs:.2f}s")}
+    peaks, kind = load_peaks()
+    peaks.update(tensor_peaks)
+    rl, rl_all = ssj_rooflines(st, peaks, slot_ms, st["light_candidates"], st["count_light_pairs"])
+    ctx.close()
+    return {
+        "metric": "ssj_pairs_per_sec", "value": out / (mean_ms * 1e-3), "unit": "pairs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_tuples": wl["n"], "c_min": c_min,
+                   "order": "count descending, ties in (x, z) order",
+                   "query": "SSJ: (a, c, |R[a] ∩ R[c]|) with |R[a] ∩ R[c]| >= c_min",
+                   "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
+                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": out,
+                   "light_candidates": st["light_candidates"], "x_ranges": st["count_ranges"],
+                   "light_pairs": st["count_light_pairs"], "heavy_pairs": st["heavy_pairs"],
+                   "l2": "256 MiB flush written before every step",
+                   "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
+        "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base,
+        "e2e": None, "e2e_note": "not measured for this workload",
+        "gpu_launches": st["kernel_launches"] * args.steps, "clocks": clocks, "parity": parity,
+    }
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
     rx, ry, wl = make_workload(args.workload)
@@ -562,6 +697,8 @@ def main():
     from paper_2002_12459_gb300 import workloads as W
     if W.WORKLOADS[args.workload]["kind"] == "star":
         res = run_star(args) if rank == 0 else None
+    elif W.WORKLOADS[args.workload]["kind"] == "ssj":
+        res = run_ssj(args) if rank == 0 else None
     else:
         res = run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -109,13 +109,20 @@ typedef struct {
                                   3 matrix build, 4 heavy GEMM kernel, 5 light
                                   classification, 6-9 light kernels (warp sort,
                                   bucket sort, merge, bitmap+union), 10 output count,
-                                  11 output placement kernel, 12 whole query */
+                                  11 output placement kernel, 12 whole query; for
+                                  jp_two_path_counts 4 is the counting product, and 13
+                                  candidate fill, 14 sort and run lengths, 15 heavy rows,
+                                  merge and output, each summed over the x ranges */
     int64_t learned_judged;    /* JP_LEARNED only: 1 the model's thresholds were used, 2 the cost
                                   model judged them too costly (modelled cost above 3 x that of
                                   Algorithm 3's thresholds) and Algorithm 3's were used; else 0 */
     int64_t filter_pairs;      /* jp_two_path_filter only: distinct candidate pairs of T */
     int64_t filter_query_out;  /* jp_two_path_filter only: |OUT| of the query on the reduced R and S
                                   (out_count is then the number of pairs of T answered) */
+    int64_t count_ranges;      /* jp_two_path_counts only: ranges of x whose light candidates were
+                                  sorted in one pass each (ms_pass[13..15] sum their phases) */
+    int64_t count_light_pairs; /* jp_two_path_counts only: distinct (x, z) among the light candidates
+                                  (heavy_pairs: nonzero entries of the heavy product) */
 } jp_stats;
 
 typedef void* (*jp_alloc_fn)(size_t bytes, void* stream, void* user);

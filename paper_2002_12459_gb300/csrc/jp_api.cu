@@ -528,6 +528,12 @@ int jp_two_path_counts(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int64_t c_
         s.learned_judged = judged;
         s.kernel_launches = jp::g_launches - launches0;
         for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
+        s.ms_pass[13] = cr.ms_fill;
+        s.ms_pass[14] = cr.ms_sort;
+        s.ms_pass[15] = cr.ms_merge;
+        s.count_ranges = cr.ranges;
+        s.count_light_pairs = cr.light_pairs;
+        s.heavy_pairs = cr.heavy_pairs;
         s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         ctx->have_stats = true;
         ctx->err.clear();

@@ -29,56 +29,61 @@ namespace {
 inline int G(int64_t n) { return grid_for(n, 256, 152 * 16); }
 inline int GW(int64_t n) { return grid_for(n * 32, 256, 152 * 16); }   // a warp per item
 
-// candidates of x: sum over its y of |S[y]|, or of |light z of S[y]| when (x, y) is heavy
-__global__ void cand_count_kernel(const int32_t* __restrict__ rxoff, const int32_t* __restrict__ rycol,
-                                  int64_t nx, const int32_t* __restrict__ hx,
-                                  const int32_t* __restrict__ hy, const int32_t* __restrict__ syoff,
-                                  const int32_t* __restrict__ sloff, int64_t* __restrict__ cnt) {
+// per entry k = (x, y) of R: the length of the list its candidates come from -- S[y], or
+// the light z of S[y] when (x, y) is heavy -- and its x; a warp per x
+__global__ void entry_count_kernel(const int32_t* __restrict__ rxoff, const int32_t* __restrict__ rycol,
+                                   int64_t nx, const int32_t* __restrict__ hx,
+                                   const int32_t* __restrict__ hy, const int32_t* __restrict__ syoff,
+                                   const int32_t* __restrict__ sloff, int64_t* __restrict__ ecnt,
+                                   int32_t* __restrict__ rowx) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nx; x += nw) {
         const bool ah = hx[x] >= 0;
-        int64_t s = 0;
         for (int32_t k = rxoff[x] + lane; k < rxoff[x + 1]; k += 32) {
             const int32_t b = rycol[k];
             const int32_t j = ah ? hy[b] : -1;
-            s += (j >= 0) ? (sloff[j + 1] - sloff[j]) : (syoff[b + 1] - syoff[b]);
+            ecnt[k] = (j >= 0) ? (sloff[j + 1] - sloff[j]) : (syoff[b + 1] - syoff[b]);
+            rowx[k] = (int32_t)x;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) cnt[x] = s;
     }
 }
 
-// the candidates of x in [x0, x1) as keys (x - x0) << 32 | z, at coff[x] - coff[x0]
-__global__ void cand_fill_kernel(int64_t x0, int64_t x1, const int64_t* __restrict__ coff,
-                                 const int32_t* __restrict__ rxoff, const int32_t* __restrict__ rycol,
+// coff[x] = offset of x's first candidate (eoff at its first entry)
+__global__ void row_offsets_kernel(const int32_t* __restrict__ rxoff, int64_t nx,
+                                   const int64_t* __restrict__ eoff, int64_t* __restrict__ coff) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= nx;
+         x += (int64_t)gridDim.x * blockDim.x)
+        coff[x] = eoff[rxoff[x]];
+}
+
+// the candidates of the entries [k0, k1) (the x range [x0, x1)) as keys (x - x0) << 32 | z,
+// entry k's at eoff[k] - eoff[k0]; a warp per entry, lanes over its list
+__global__ void cand_fill_kernel(int64_t k0, int64_t k1, int64_t x0, const int64_t* __restrict__ eoff,
+                                 const int32_t* __restrict__ rowx, const int32_t* __restrict__ rycol,
                                  const int32_t* __restrict__ hx, const int32_t* __restrict__ hy,
                                  const int32_t* __restrict__ syoff, const int32_t* __restrict__ szcol,
                                  const int32_t* __restrict__ sloff, const int32_t* __restrict__ slcol,
                                  uint64_t* __restrict__ keys) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t c0 = coff[x0];
-    for (int64_t x = x0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); x < x1; x += nw) {
-        int64_t base = coff[x] - c0;
-        const bool ah = hx[x] >= 0;
-        const uint64_t hi = (uint64_t)(x - x0) << 32;
-        for (int32_t k = rxoff[x]; k < rxoff[x + 1]; ++k) {
-            const int32_t b = rycol[k];
-            const int32_t j = ah ? hy[b] : -1;
-            const int32_t* list;
-            int32_t len;
-            if (j >= 0) {
-                list = slcol + sloff[j];
-                len = sloff[j + 1] - sloff[j];
-            } else {
-                list = szcol + syoff[b];
-                len = syoff[b + 1] - syoff[b];
-            }
-            for (int32_t e = lane; e < len; e += 32) keys[base + e] = hi | (uint32_t)list[e];
-            base += len;
+    const int64_t c0 = eoff[k0];
+    for (int64_t k = k0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < k1; k += nw) {
+        const int32_t x = rowx[k];
+        const int32_t b = rycol[k];
+        const int32_t j = hx[x] >= 0 ? hy[b] : -1;
+        const int32_t* list;
+        int32_t len;
+        if (j >= 0) {
+            list = slcol + sloff[j];
+            len = sloff[j + 1] - sloff[j];
+        } else {
+            list = szcol + syoff[b];
+            len = syoff[b + 1] - syoff[b];
         }
+        uint64_t* dst = keys + (eoff[k] - c0);
+        const uint64_t hi = (uint64_t)(x - x0) << 32;
+        for (int32_t e = lane; e < len; e += 32) dst[e] = hi | (uint32_t)list[e];
     }
 }
 
@@ -155,43 +160,56 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n,
     return lo;
 }
 
-// heavy pairs already among the light pairs add their count there; the rest are flagged
-__global__ void merge_probe_kernel(const uint64_t* __restrict__ hk, const uint32_t* __restrict__ hc,
-                                   int64_t nh, const uint64_t* __restrict__ lk, uint32_t* lc,
-                                   int64_t nl, uint32_t* __restrict__ flag) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nh;
+// A light pair (x, z) with x and z heavy takes the heavy product's entry into its count and
+// clears it, so that the entries left in the count matrix are the pairs with heavy witnesses
+// only.  Keys are distinct, so each entry is read by at most one thread.
+__global__ void heavy_absorb_kernel(const uint64_t* __restrict__ uk, uint32_t* __restrict__ lc,
+                                    int64_t m, int64_t x0, const int32_t* __restrict__ hx,
+                                    const int32_t* __restrict__ hz, uint32_t* __restrict__ C,
+                                    int64_t ldc, unsigned long long* __restrict__ absorbed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = lower_bound_u64(lk, nl, hk[i]);
-        if (p < nl && lk[p] == hk[i]) {
-            lc[p] += hc[i];          // keys are distinct within each list: one writer per p
-            flag[i] = 0u;
-        } else {
-            flag[i] = 1u;
+        const uint64_t k = uk[i];
+        const int32_t h = hx[x0 + (int64_t)(k >> 32)];
+        bool took = false;
+        if (h >= 0) {
+            const int32_t c = hz[(uint32_t)k];
+            if (c >= 0) {
+                uint32_t* e = C + (int64_t)h * ldc + c;
+                const uint32_t v = *e;
+                if (v != 0u) {
+                    lc[i] += v;
+                    *e = 0u;
+                    took = true;
+                }
+            }
         }
+        const unsigned b = __ballot_sync(__activemask(), took);
+        if (took && (threadIdx.x & 31) == __ffs(b) - 1) atomicAdd(absorbed, (unsigned long long)__popc(b));
     }
 }
 
-__global__ void compact_kv_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c,
-                                  int64_t n, const uint32_t* __restrict__ flag,
-                                  const uint32_t* __restrict__ pos, uint64_t* __restrict__ ok,
-                                  uint32_t* __restrict__ oc) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (flag[i]) {
-            ok[pos[i]] = k[i];
-            oc[pos[i]] = c[i];
-        }
+// first index of row r (keys (r << 32) | z, sorted) for r = 0..rows
+__global__ void row_bounds_kernel(const uint64_t* __restrict__ k, int64_t n, int64_t rows,
+                                  int64_t* __restrict__ bound) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= rows;
+         r += (int64_t)gridDim.x * blockDim.x)
+        bound[r] = lower_bound_u64(k, n, (uint64_t)r << 32);
 }
 
-// merge of two sorted lists with no key in common: element i of a goes to
-// i + (number of b keys below it)
-__global__ void merge_place_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ac,
-                                   int64_t na, const uint64_t* __restrict__ bk, int64_t nb,
-                                   uint64_t* __restrict__ ok, uint32_t* __restrict__ oc) {
+// merge of two sorted lists with no key in common: element i of a goes to i + (number of b
+// keys below it), counted within its own row of b
+__global__ void merge_rows_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ac,
+                                  int64_t na, const uint64_t* __restrict__ bk,
+                                  const int64_t* __restrict__ brow, uint64_t* __restrict__ ok,
+                                  uint32_t* __restrict__ oc) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = i + lower_bound_u64(bk, nb, ak[i]);
-        ok[p] = ak[i];
+        const uint64_t key = ak[i];
+        const int64_t r = (int64_t)(key >> 32);
+        const int64_t s0 = brow[r];
+        const int64_t p = i + s0 + lower_bound_u64(bk + s0, brow[r + 1] - s0, key);
+        ok[p] = key;
         oc[p] = ac[i];
     }
 }
@@ -281,14 +299,23 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
         heavy_gemm_counts(h, C, d_status, st);
     }
 
-    // light candidates per x and their offsets
-    int64_t* cnt = ws.get<int64_t>(nx + 1);
+    // light candidates per entry of R, their offsets, and per x
+    const int64_t nr = g.nr;
+    int64_t* ecnt = ws.get<int64_t>(nr + 1);
+    int64_t* eoff = ws.get<int64_t>(nr + 1);
+    int32_t* rowx = ws.get<int32_t>(nr + 1);
     int64_t* coff = ws.get<int64_t>(nx + 1);
-    cand_count_kernel<<<GW(nx), 256, 0, st>>>(g.rxoff, g.rycol, nx, p.hx, p.hy, g.syoff, p.sloff, cnt);
+    entry_count_kernel<<<GW(nx), 256, 0, st>>>(g.rxoff, g.rycol, nx, p.hx, p.hy, g.syoff, p.sloff,
+                                               ecnt, rowx);
     JP_CHECK_LAUNCH();
-    scan_i64(cnt, coff, nx, coff + nx, ws, st);
+    scan_i64(ecnt, eoff, nr, eoff + nr, ws, st);
+    row_offsets_kernel<<<G(nx + 1), 256, 0, st>>>(g.rxoff, nx, eoff, coff);
+    JP_CHECK_LAUNCH();
     std::vector<int64_t> hoff_host((size_t)nx + 1);
+    std::vector<int32_t> rxoff_host((size_t)nx + 1);
     JP_CUDA_TRY(cudaMemcpyAsync(hoff_host.data(), coff, (nx + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, st));
+    JP_CUDA_TRY(cudaMemcpyAsync(rxoff_host.data(), g.rxoff, (nx + 1) * sizeof(int32_t),
                                 cudaMemcpyDeviceToHost, st));
     std::vector<int32_t> hx_inv_host((size_t)p.u);
     if (p.u > 0)
@@ -311,12 +338,26 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
     uint32_t* start = ws.get<uint32_t>(cap);
     uint32_t* lc = ws.get<uint32_t>(cap);
     uint32_t* d_total = ws.get<uint32_t>(1);
-    Grow<uint32_t> hnnz, hoffs, hflag, hpos, hc, h2c, mc, kflag, kpos;
-    Grow<uint64_t> hk, h2k, mk;
+    unsigned long long* d_absorbed = ws.get<unsigned long long>(1);
+    JP_CUDA_TRY(cudaMemsetAsync(d_absorbed, 0, sizeof(unsigned long long), st));
+    Grow<uint32_t> hnnz, hoffs, hc, mc, kflag, kpos;
+    Grow<uint64_t> hk, mk;
+    Grow<int64_t> lrow, hrow;
 
     struct Piece { int32_t* x; int32_t* z; int32_t* c; int64_t n; };
     std::vector<Piece> pieces;
     int64_t total = 0;
+    // device time of the phases of every range: fill | sort and run lengths | heavy rows and merge
+    struct Events {
+        cudaEvent_t e[4] = {};
+        Events() { for (auto& x : e) cudaEventCreate(&x); }
+        ~Events() { for (auto& x : e) cudaEventDestroy(x); }
+    } ev;
+    auto elapsed = [](cudaEvent_t a, cudaEvent_t b) {
+        float v = 0;
+        if (cudaEventElapsedTime(&v, a, b) != cudaSuccess) { cudaGetLastError(); v = 0; }
+        return (double)v;
+    };
     for (int64_t x0 = 0; x0 < nx;) {
         // the longest range of x from x0 whose candidates fit the scratch
         int64_t x1 = std::upper_bound(hoff_host.begin() + x0 + 1, hoff_host.end(),
@@ -325,10 +366,14 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
         const int64_t nc = hoff_host[x1] - hoff_host[x0];
         // light pairs of the range: sorted keys, run lengths
         int64_t m = 0;
+        JP_CUDA_TRY(cudaEventRecord(ev.e[0], st));
+        JP_CUDA_TRY(cudaEventRecord(ev.e[1], st));
         if (nc > 0) {
-            cand_fill_kernel<<<GW(x1 - x0), 256, 0, st>>>(x0, x1, coff, g.rxoff, g.rycol, p.hx, p.hy,
+            const int64_t k0 = rxoff_host[x0], k1 = rxoff_host[x1];
+            cand_fill_kernel<<<GW(k1 - k0), 256, 0, st>>>(k0, k1, x0, eoff, rowx, g.rycol, p.hx, p.hy,
                                                           g.syoff, g.szcol, p.sloff, p.slcol, keys);
             JP_CHECK_LAUNCH();
+            JP_CUDA_TRY(cudaEventRecord(ev.e[1], st));
             uint64_t* s = radix_sort_u64(keys, tmp, nc, ws, st, hist_host);
             run_mark_kernel<<<G(nc), 256, 0, st>>>(s, nc, flag);
             JP_CHECK_LAUNCH();
@@ -339,14 +384,22 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
             run_length_kernel<<<G(m), 256, 0, st>>>(start, m, nc, lc);
             JP_CHECK_LAUNCH();
         }
+        JP_CUDA_TRY(cudaEventRecord(ev.e[2], st));
         // heavy pairs of the range: rows h0..h1 of the count matrix
         const int64_t h0 = std::lower_bound(hx_inv_host.begin(), hx_inv_host.end(), (int32_t)x0) -
                            hx_inv_host.begin();
         const int64_t h1 = std::lower_bound(hx_inv_host.begin(), hx_inv_host.end(),
                                             (int32_t)std::min<int64_t>(x1, 0x7fffffff)) -
                            hx_inv_host.begin();
+        // heavy entries: those of light pairs are added to them and cleared; the rest (pairs
+        // with heavy witnesses only) are compacted to keys and merged in
         int64_t nh = 0;
         if (C && h1 > h0) {
+            if (m > 0) {
+                heavy_absorb_kernel<<<G(m), 256, 0, st>>>(uk, lc, m, x0, p.hx, p.hz, C, h.w_pad,
+                                                          d_absorbed);
+                JP_CHECK_LAUNCH();
+            }
             uint32_t* nnz = hnnz.need(h1 - h0, ws);
             uint32_t* off = hoffs.need(h1 - h0, ws);
             heavy_nnz_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, nnz);
@@ -360,39 +413,28 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
                 JP_CHECK_LAUNCH();
             }
         }
-        // merge: equal keys summed into the light list, the others placed between
         const uint64_t* fk = uk;
         const uint32_t* fc = lc;
         int64_t nf = m;
         if (nh > 0) {
-            uint32_t* hf = hflag.need(nh, ws);
-            uint32_t* hp = hpos.need(nh, ws);
+            const int64_t rows = x1 - x0;
+            int64_t* lr = lrow.need(rows + 1, ws);
+            int64_t* hr = hrow.need(rows + 1, ws);
+            row_bounds_kernel<<<G(rows + 1), 256, 0, st>>>(uk, m, rows, lr);
+            JP_CHECK_LAUNCH();
+            row_bounds_kernel<<<G(rows + 1), 256, 0, st>>>(hk.p, nh, rows, hr);
+            JP_CHECK_LAUNCH();
+            uint64_t* ok = mk.need(m + nh, ws);
+            uint32_t* oc = mc.need(m + nh, ws);
             if (m > 0) {
-                merge_probe_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, uk, lc, m, hf);
-                JP_CHECK_LAUNCH();
-            } else {
-                keep_flag_kernel<<<G(nh), 256, 0, st>>>(hc.p, nh, 1u, hf);   // every entry is >= 1
+                merge_rows_kernel<<<G(m), 256, 0, st>>>(uk, lc, m, hk.p, hr, ok, oc);
                 JP_CHECK_LAUNCH();
             }
-            scan_u32(hf, hp, nh, d_total, ws, st);
-            const int64_t nh2 = read1(d_total, st);
-            if (nh2 > 0) {
-                uint64_t* k2 = h2k.need(nh2, ws);
-                uint32_t* c2 = h2c.need(nh2, ws);
-                compact_kv_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, hf, hp, k2, c2);
-                JP_CHECK_LAUNCH();
-                uint64_t* ok = mk.need(m + nh2, ws);
-                uint32_t* oc = mc.need(m + nh2, ws);
-                if (m > 0) {
-                    merge_place_kernel<<<G(m), 256, 0, st>>>(uk, lc, m, k2, nh2, ok, oc);
-                    JP_CHECK_LAUNCH();
-                }
-                merge_place_kernel<<<G(nh2), 256, 0, st>>>(k2, c2, nh2, uk, m, ok, oc);
-                JP_CHECK_LAUNCH();
-                fk = ok;
-                fc = oc;
-                nf = m + nh2;
-            }
+            merge_rows_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, uk, lr, ok, oc);
+            JP_CHECK_LAUNCH();
+            fk = ok;
+            fc = oc;
+            nf = m + nh;
         }
         // pairs counted at least c_min
         if (nf > 0) {
@@ -411,8 +453,17 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
                 total += nk;
             }
         }
+        out.light_pairs += m;
+        out.heavy_pairs += nh;          // heavy-only pairs; the absorbed ones are added below
+        JP_CUDA_TRY(cudaEventRecord(ev.e[3], st));
+        JP_CUDA_TRY(cudaEventSynchronize(ev.e[3]));
+        out.ms_fill += elapsed(ev.e[0], ev.e[1]);
+        out.ms_sort += elapsed(ev.e[1], ev.e[2]);
+        out.ms_merge += elapsed(ev.e[2], ev.e[3]);
+        ++out.ranges;
         x0 = x1;
     }
+    out.heavy_pairs += (int64_t)read1(d_absorbed, st);
     if (total >= ((int64_t)1 << 32)) throw Error{JP_EUNSUPPORTED, "2^32 or more result pairs"};
     // the pieces one after another
     int32_t* X = ws.get<int32_t>(total + 1);

@@ -220,6 +220,10 @@ struct CountResult {
     int32_t* cnt = nullptr;
     int64_t n = 0;
     int64_t candidates = 0;
+    double ms_fill = 0, ms_sort = 0, ms_merge = 0;   // device ms summed over the x ranges
+    int64_t ranges = 0;
+    int64_t light_pairs = 0;     // distinct (x, z) among the light candidates
+    int64_t heavy_pairs = 0;     // nonzero entries of the heavy product
 };
 void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_min, int order,
                  CountResult& out, Arena& ws, cudaStream_t st, uint32_t* d_status,

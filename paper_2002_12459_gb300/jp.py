@@ -56,7 +56,8 @@ class jp_stats(ctypes.Structure):
                 ("light_deg", ctypes.c_int64 * 8),
                 ("ms_total", ctypes.c_double),
                 ("ms_pass", ctypes.c_double * 16), ("learned_judged", ctypes.c_int64),
-                ("filter_pairs", ctypes.c_int64), ("filter_query_out", ctypes.c_int64)]
+                ("filter_pairs", ctypes.c_int64), ("filter_query_out", ctypes.c_int64),
+                ("count_ranges", ctypes.c_int64), ("count_light_pairs", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

@@ -250,6 +250,10 @@ WORKLOADS = {
     "two_path_powerlaw_1m": dict(kind="two_path", gen="powerlaw", n=1_000_000,
                                  dom_x=200_000, gamma_x=2.1,
                                  dom_y=100_000, gamma_y=1.8, seed=0),
+    # set similarity join on the 10M relation: pairs sharing >= 2 y, by decreasing count
+    "ssj_powerlaw_10m": dict(kind="ssj", gen="powerlaw", n=10_000_000,
+                             dom_x=2_000_000, gamma_x=2.1,
+                             dom_y=1_000_000, gamma_y=1.8, seed=0, c_min=2),
     # star k = 3, 3 x 2M tuples, shared y domain 200k gamma 1.5, x uniform 500k
     "star3_2m": dict(kind="star", gen="star", k=3, n=2_000_000, dom_x=500_000,
                      dom_y=200_000, gamma_y=1.5, seed=0),

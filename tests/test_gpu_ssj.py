@@ -59,7 +59,11 @@ def test_counts_random_relations(ctx, oracle_mod, seed, mode, d):
     ctx.set_threshold(mode, d, d)
     for c_min, order in [(1, "pairs"), (2, "count"), (5, "pairs")]:
         n = check(ctx, oracle_mod, R, S, c_min, order)
-        assert n > 0 and ctx.stats()["out_count"] == n
+        st = ctx.stats()
+        assert n > 0 and st["out_count"] == n
+        if c_min == 1:      # every pair has a light or a heavy witness, or both
+            lp, hp = st["count_light_pairs"], st["heavy_pairs"]
+            assert max(lp, hp) <= n <= lp + hp
     if mode == "fixed" and d == 1:
         assert ctx.stats()["u"] > 0
 
