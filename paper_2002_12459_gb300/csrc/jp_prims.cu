@@ -162,43 +162,84 @@ __global__ void rs_upsweep_kernel(const uint64_t* keys, int64_t n, int shift, ui
     counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Stable scatter of one tile: keys are ranked round by round (a round is 256
-// consecutive keys, one per thread in index order); within a round the warps
-// rank with __match_any_sync and a per-digit prefix across warps.
-__global__ void rs_downsweep_kernel(const uint64_t* in, uint64_t* out, int64_t n, int shift,
-                                    const uint32_t* offs, int64_t nblocks) {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wc[2][8][256];
+// Stable scatter of one tile of RS_TILE keys.  Warp w owns the keys
+// [w * 512, (w + 1) * 512) of the tile and ranks them round by round (32
+// consecutive keys a round) with __match_any_sync against a warp-private
+// counter per digit; the per-warp counts then give every key its position in
+// the tile sorted by digit (warps in order, so the order of equal digits is
+// the input order).  The keys are placed there in shared memory and written
+// out in that order: runs of one digit go to consecutive addresses.
+__global__ void __launch_bounds__(RS_THREADS) rs_downsweep_kernel(const uint64_t* in, uint64_t* out,
+                                                                  int64_t n, int shift,
+                                                                  const uint32_t* offs, int64_t nblocks) {
+    __shared__ uint64_t sk[RS_TILE];
+    __shared__ uint32_t cnt[RS_THREADS / 32][256];
+    __shared__ uint32_t lstart[256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t wsum[RS_THREADS / 32];
+    constexpr int WARPS = RS_THREADS / 32;
+    constexpr int PER_WARP = RS_TILE / WARPS;   // = 32 * RS_ITEMS
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    base[t] = offs[(int64_t)t * nblocks + blockIdx.x];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) { wc[0][w][t] = 0; wc[1][w][t] = 0; }
+    for (int w = 0; w < WARPS; ++w) cnt[w][t] = 0u;
+    gbase[t] = offs[(int64_t)t * nblocks + blockIdx.x];
     __syncthreads();
     const int64_t tb = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t wb = tb + (int64_t)warp * PER_WARP;
     const unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        const int buf = r & 1;
-        int64_t idx = tb + (int64_t)r * RS_THREADS + t;
-        bool valid = idx < n;
-        uint64_t k = valid ? in[idx] : 0ull;
-        unsigned d = valid ? (unsigned)((k >> shift) & 255) : (256u + lane);
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        unsigned rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[buf][warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t s = base[t];
+    uint64_t k[RS_ITEMS];
+    uint32_t rk[RS_ITEMS];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                uint32_t c = wc[buf][w][t];
-                wc[buf][w][t] = s;
-                s += c;
-                wc[buf ^ 1][w][t] = 0;
-            }
-            base[t] = s;
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t idx = wb + r * 32 + lane;
+        k[r] = idx < n ? in[idx] : 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const bool valid = wb + r * 32 + lane < n;
+        const unsigned d = valid ? (unsigned)((k[r] >> shift) & 255) : (256u + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? cnt[warp][d] : 0u;
+        rk[r] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0u) cnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit t: where each warp's keys of that digit start among the tile's, and the tile's total
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = cnt[w][t];
+        cnt[w][t] = tot;
+        tot += c;
+    }
+    // exclusive scan of the totals over the 256 digits
+    uint32_t v = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    lstart[t] = wpre + v - tot;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        if (wb + r * 32 + lane < n) {
+            const unsigned d = (unsigned)((k[r] >> shift) & 255);
+            sk[lstart[d] + cnt[warp][d] + rk[r]] = k[r];
         }
-        __syncthreads();
-        if (valid) out[wc[buf][warp][d] + rank] = k;
+    }
+    __syncthreads();
+    const int tile_n = (int)((n - tb) < RS_TILE ? (n - tb) : RS_TILE);
+    for (int i = t; i < tile_n; i += RS_THREADS) {
+        const uint64_t key = sk[i];
+        const unsigned d = (unsigned)((key >> shift) & 255);
+        out[gbase[d] + (uint32_t)(i - (int)lstart[d])] = key;
     }
 }
 
