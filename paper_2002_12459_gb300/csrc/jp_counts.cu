@@ -104,30 +104,37 @@ __global__ void run_start_kernel(const uint64_t* __restrict__ k, int64_t n,
         }
 }
 
-__global__ void run_length_kernel(const uint32_t* __restrict__ start, int64_t m, int64_t n,
-                                  uint32_t* __restrict__ cnt) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
-         j += (int64_t)gridDim.x * blockDim.x)
-        cnt[j] = (j + 1 < m ? start[j + 1] : (uint32_t)n) - start[j];
-}
-
-// nonzero entries of the heavy rows [h0, h1) of the count matrix; a warp per row
+// nonzero entries of the heavy rows [h0, h1) of the count matrix (added to *nonzero) and,
+// per row, those of at least c_min; a warp per row
 __global__ void heavy_nnz_kernel(const uint32_t* __restrict__ C, int64_t ldc, int64_t h0, int64_t h1,
-                                 int64_t w, uint32_t* __restrict__ nnz) {
+                                 int64_t w, uint32_t c_min, uint32_t* __restrict__ keep,
+                                 unsigned long long* __restrict__ nonzero) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t h = h0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); h < h1; h += nw) {
         const uint32_t* row = C + h * ldc;
-        uint32_t s = 0;
-        for (int64_t j = lane; j < w; j += 32) s += row[j] != 0u;
+        uint32_t s = 0, z = 0;
+        for (int64_t j = lane; j < w; j += 32) {
+            const uint32_t v = row[j];
+            s += v >= c_min;
+            z += v != 0u;
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) nnz[h - h0] = s;
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_down_sync(0xffffffffu, s, o);
+            z += __shfl_down_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) {
+            keep[h - h0] = s;
+            if (z) atomicAdd(nonzero, (unsigned long long)z);
+        }
     }
 }
 
+// the entries of at least c_min (c_min >= 1) of the heavy rows [h0, h1) as keys
+// (x - x0) << 32 | z and counts, row after row, at off[h - h0]
 __global__ void heavy_keys_kernel(const uint32_t* __restrict__ C, int64_t ldc, int64_t h0, int64_t h1,
-                                  int64_t w, const int32_t* __restrict__ hx_inv,
+                                  int64_t w, uint32_t c_min, const int32_t* __restrict__ hx_inv,
                                   const int32_t* __restrict__ hz_inv, int64_t x0,
                                   const uint32_t* __restrict__ off, uint64_t* __restrict__ keys,
                                   uint32_t* __restrict__ cnt) {
@@ -140,8 +147,9 @@ __global__ void heavy_keys_kernel(const uint32_t* __restrict__ C, int64_t ldc, i
         for (int64_t j0 = 0; j0 < w; j0 += 32) {
             const int64_t j = j0 + lane;
             const uint32_t v = j < w ? row[j] : 0u;
-            const unsigned m = __ballot_sync(0xffffffffu, v != 0u);
-            if (v != 0u) {
+            const bool kept = v >= c_min && v != 0u;
+            const unsigned m = __ballot_sync(0xffffffffu, kept);
+            if (kept) {
                 const uint32_t p = base + __popc(m & ((1u << lane) - 1u));
                 keys[p] = hi | (uint32_t)hz_inv[j];
                 cnt[p] = v;
@@ -160,30 +168,38 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t* a, int64_t n,
     return lo;
 }
 
-// A light pair (x, z) with x and z heavy takes the heavy product's entry into its count and
-// clears it, so that the entries left in the count matrix are the pairs with heavy witnesses
-// only.  Keys are distinct, so each entry is read by at most one thread.
-__global__ void heavy_absorb_kernel(const uint64_t* __restrict__ uk, uint32_t* __restrict__ lc,
-                                    int64_t m, int64_t x0, const int32_t* __restrict__ hx,
-                                    const int32_t* __restrict__ hz, uint32_t* __restrict__ C,
-                                    int64_t ldc, unsigned long long* __restrict__ absorbed) {
+// The count of light pair j (the run length of its key among the sorted candidates) plus,
+// for x and z heavy, the heavy product's entry, which is then cleared: the entries left in
+// the count matrix are the pairs with heavy witnesses only.  Keys are distinct, so each entry
+// is read by at most one thread.  keep[j] = count >= c_min.
+__global__ void light_count_kernel(const uint64_t* __restrict__ uk, const uint32_t* __restrict__ start,
+                                   int64_t m, int64_t nc, int64_t x0, const int32_t* __restrict__ hx,
+                                   const int32_t* __restrict__ hz, uint32_t* __restrict__ C,
+                                   int64_t ldc, uint32_t c_min, uint32_t* __restrict__ lc,
+                                   uint32_t* __restrict__ keep,
+                                   unsigned long long* __restrict__ absorbed) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = uk[i];
-        const int32_t h = hx[x0 + (int64_t)(k >> 32)];
+        uint32_t c = (i + 1 < m ? start[i + 1] : (uint32_t)nc) - start[i];
         bool took = false;
-        if (h >= 0) {
-            const int32_t c = hz[(uint32_t)k];
-            if (c >= 0) {
-                uint32_t* e = C + (int64_t)h * ldc + c;
-                const uint32_t v = *e;
-                if (v != 0u) {
-                    lc[i] += v;
-                    *e = 0u;
-                    took = true;
+        if (C) {
+            const uint64_t k = uk[i];
+            const int32_t h = hx[x0 + (int64_t)(k >> 32)];
+            if (h >= 0) {
+                const int32_t zc = hz[(uint32_t)k];
+                if (zc >= 0) {
+                    uint32_t* e = C + (int64_t)h * ldc + zc;
+                    const uint32_t v = *e;
+                    if (v != 0u) {
+                        c += v;
+                        *e = 0u;
+                        took = true;
+                    }
                 }
             }
         }
+        lc[i] = c;
+        keep[i] = c >= c_min ? 1u : 0u;
         const unsigned b = __ballot_sync(__activemask(), took);
         if (took && (threadIdx.x & 31) == __ffs(b) - 1) atomicAdd(absorbed, (unsigned long long)__popc(b));
     }
@@ -197,44 +213,50 @@ __global__ void row_bounds_kernel(const uint64_t* __restrict__ k, int64_t n, int
         bound[r] = lower_bound_u64(k, n, (uint64_t)r << 32);
 }
 
-// merge of two sorted lists with no key in common: element i of a goes to i + (number of b
-// keys below it), counted within its own row of b
-__global__ void merge_rows_kernel(const uint64_t* __restrict__ ak, const uint32_t* __restrict__ ac,
-                                  int64_t na, const uint64_t* __restrict__ bk,
-                                  const int64_t* __restrict__ brow, uint64_t* __restrict__ ok,
-                                  uint32_t* __restrict__ oc) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na;
+// Output of the kept light pairs: pair i goes to (kept light pairs before it, pos[i]) +
+// (heavy-only pairs below its key, counted within its row of the heavy list; none when nh = 0)
+__global__ void out_light_kernel(const uint64_t* __restrict__ uk, const uint32_t* __restrict__ lc,
+                                 const uint32_t* __restrict__ keep, const uint32_t* __restrict__ pos,
+                                 int64_t m, const uint64_t* __restrict__ hk,
+                                 const int64_t* __restrict__ hrow, int64_t x0,
+                                 const int32_t* __restrict__ xval, const int32_t* __restrict__ zval,
+                                 int32_t* __restrict__ ox, int32_t* __restrict__ oz,
+                                 int32_t* __restrict__ oc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = ak[i];
+        if (!keep[i]) continue;
+        const uint64_t key = uk[i];
         const int64_t r = (int64_t)(key >> 32);
-        const int64_t s0 = brow[r];
-        const int64_t p = i + s0 + lower_bound_u64(bk + s0, brow[r + 1] - s0, key);
-        ok[p] = key;
-        oc[p] = ac[i];
+        int64_t p = pos[i];
+        if (hrow) {
+            const int64_t s0 = hrow[r];
+            p += s0 + lower_bound_u64(hk + s0, hrow[r + 1] - s0, key);
+        }
+        ox[p] = xval[x0 + r];
+        oz[p] = zval[(uint32_t)key];
+        oc[p] = (int32_t)lc[i];
     }
 }
 
-__global__ void keep_flag_kernel(const uint32_t* __restrict__ c, int64_t n, uint32_t c_min,
-                                 uint32_t* __restrict__ flag) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        flag[i] = c[i] >= c_min ? 1u : 0u;
-}
-
-__global__ void write_pairs_kernel(const uint64_t* __restrict__ k, const uint32_t* __restrict__ c,
-                                   int64_t n, const uint32_t* __restrict__ flag,
-                                   const uint32_t* __restrict__ pos, int64_t x0,
-                                   const int32_t* __restrict__ xval, const int32_t* __restrict__ zval,
-                                   int32_t* __restrict__ ox, int32_t* __restrict__ oz,
-                                   int32_t* __restrict__ oc) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (flag[i]) {
-            const uint32_t p = pos[i];
-            ox[p] = xval[x0 + (int64_t)(k[i] >> 32)];
-            oz[p] = zval[(uint32_t)k[i]];
-            oc[p] = (int32_t)c[i];
-        }
+// Output of the heavy-only pairs (all kept): pair i goes to i + (kept light pairs below its
+// key: pos at its insertion point in the light list, found within its row)
+__global__ void out_heavy_kernel(const uint64_t* __restrict__ hk, const uint32_t* __restrict__ hc,
+                                 int64_t nh, const uint64_t* __restrict__ uk,
+                                 const int64_t* __restrict__ lrow, const uint32_t* __restrict__ pos,
+                                 int64_t x0, const int32_t* __restrict__ xval,
+                                 const int32_t* __restrict__ zval, int32_t* __restrict__ ox,
+                                 int32_t* __restrict__ oz, int32_t* __restrict__ oc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nh;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = hk[i];
+        const int64_t r = (int64_t)(key >> 32);
+        const int64_t s0 = lrow[r];
+        const int64_t q = s0 + lower_bound_u64(uk + s0, lrow[r + 1] - s0, key);
+        const int64_t p = i + pos[q];
+        ox[p] = xval[x0 + r];
+        oz[p] = zval[(uint32_t)key];
+        oc[p] = (int32_t)hc[i];
+    }
 }
 
 // sort keys for decreasing count, ties in position order: (~count) << 32 | position
@@ -333,21 +355,21 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
     uint64_t* keys = ws.get<uint64_t>(cap);
     uint64_t* tmp = ws.get<uint64_t>(cap);
     uint32_t* flag = ws.get<uint32_t>(cap);
-    uint32_t* idx = ws.get<uint32_t>(cap);
+    uint32_t* idx = ws.get<uint32_t>(cap + 1);
     uint64_t* uk = ws.get<uint64_t>(cap);
     uint32_t* start = ws.get<uint32_t>(cap);
     uint32_t* lc = ws.get<uint32_t>(cap);
     uint32_t* d_total = ws.get<uint32_t>(1);
-    unsigned long long* d_absorbed = ws.get<unsigned long long>(1);
-    JP_CUDA_TRY(cudaMemsetAsync(d_absorbed, 0, sizeof(unsigned long long), st));
-    Grow<uint32_t> hnnz, hoffs, hc, mc, kflag, kpos;
-    Grow<uint64_t> hk, mk;
+    unsigned long long* d_absorbed = ws.get<unsigned long long>(2);   // absorbed, nonzero
+    JP_CUDA_TRY(cudaMemsetAsync(d_absorbed, 0, 2 * sizeof(unsigned long long), st));
+    Grow<uint32_t> hkeep, hoffs, hc;
+    Grow<uint64_t> hk;
     Grow<int64_t> lrow, hrow;
 
     struct Piece { int32_t* x; int32_t* z; int32_t* c; int64_t n; };
     std::vector<Piece> pieces;
     int64_t total = 0;
-    // device time of the phases of every range: fill | sort and run lengths | heavy rows and merge
+    // device time of the phases of every range: fill | sort and run lengths | counts and output
     struct Events {
         cudaEvent_t e[4] = {};
         Events() { for (auto& x : e) cudaEventCreate(&x); }
@@ -364,7 +386,8 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
                                       hoff_host[x0] + cap) - hoff_host.begin() - 1;
         if (x1 <= x0) x1 = x0 + 1;
         const int64_t nc = hoff_host[x1] - hoff_host[x0];
-        // light pairs of the range: sorted keys, run lengths
+        const int64_t rows = x1 - x0;
+        // light pairs of the range: sorted keys, run starts
         int64_t m = 0;
         JP_CUDA_TRY(cudaEventRecord(ev.e[0], st));
         JP_CUDA_TRY(cudaEventRecord(ev.e[1], st));
@@ -374,87 +397,79 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
                                                           g.syoff, g.szcol, p.sloff, p.slcol, keys);
             JP_CHECK_LAUNCH();
             JP_CUDA_TRY(cudaEventRecord(ev.e[1], st));
-            uint64_t* s = radix_sort_u64(keys, tmp, nc, ws, st, hist_host);
-            run_mark_kernel<<<G(nc), 256, 0, st>>>(s, nc, flag);
+            uint64_t* sk = radix_sort_u64(keys, tmp, nc, ws, st, hist_host);
+            run_mark_kernel<<<G(nc), 256, 0, st>>>(sk, nc, flag);
             JP_CHECK_LAUNCH();
             scan_u32(flag, idx, nc, d_total, ws, st);
-            run_start_kernel<<<G(nc), 256, 0, st>>>(s, nc, flag, idx, uk, start);
+            run_start_kernel<<<G(nc), 256, 0, st>>>(sk, nc, flag, idx, uk, start);
             JP_CHECK_LAUNCH();
             m = read1(d_total, st);
-            run_length_kernel<<<G(m), 256, 0, st>>>(start, m, nc, lc);
-            JP_CHECK_LAUNCH();
         }
         JP_CUDA_TRY(cudaEventRecord(ev.e[2], st));
-        // heavy pairs of the range: rows h0..h1 of the count matrix
+        // heavy rows of the range
         const int64_t h0 = std::lower_bound(hx_inv_host.begin(), hx_inv_host.end(), (int32_t)x0) -
                            hx_inv_host.begin();
         const int64_t h1 = std::lower_bound(hx_inv_host.begin(), hx_inv_host.end(),
                                             (int32_t)std::min<int64_t>(x1, 0x7fffffff)) -
                            hx_inv_host.begin();
-        // heavy entries: those of light pairs are added to them and cleared; the rest (pairs
-        // with heavy witnesses only) are compacted to keys and merged in
-        int64_t nh = 0;
-        if (C && h1 > h0) {
-            if (m > 0) {
-                heavy_absorb_kernel<<<G(m), 256, 0, st>>>(uk, lc, m, x0, p.hx, p.hz, C, h.w_pad,
-                                                          d_absorbed);
-                JP_CHECK_LAUNCH();
-            }
-            uint32_t* nnz = hnnz.need(h1 - h0, ws);
-            uint32_t* off = hoffs.need(h1 - h0, ws);
-            heavy_nnz_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, nnz);
+        const bool heavy_rows = C && h1 > h0;
+        // final counts of the light pairs (the product's entries of heavy x and z taken in and
+        // cleared), kept flags and their positions (idx[m] = kept light pairs)
+        int64_t ml = 0;
+        if (m > 0) {
+            light_count_kernel<<<G(m), 256, 0, st>>>(uk, start, m, nc, x0, p.hx, p.hz,
+                                                     heavy_rows ? C : nullptr, h.w_pad, cmin, lc, flag,
+                                                     d_absorbed);
             JP_CHECK_LAUNCH();
-            scan_u32(nnz, off, h1 - h0, d_total, ws, st);
+            scan_u32(flag, idx, m, idx + m, ws, st);
+        } else {
+            JP_CUDA_TRY(cudaMemsetAsync(idx, 0, sizeof(uint32_t), st));
+        }
+        // heavy-only pairs of at least c_min
+        int64_t nh = 0;
+        if (heavy_rows) {
+            uint32_t* kp = hkeep.need(h1 - h0, ws);
+            uint32_t* off = hoffs.need(h1 - h0, ws);
+            heavy_nnz_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, cmin, kp,
+                                                          d_absorbed + 1);
+            JP_CHECK_LAUNCH();
+            scan_u32(kp, off, h1 - h0, d_total, ws, st);
             nh = read1(d_total, st);
             if (nh > 0) {
-                heavy_keys_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, p.hx_inv,
-                                                               p.hz_inv, x0, off, hk.need(nh, ws),
-                                                               hc.need(nh, ws));
+                heavy_keys_kernel<<<GW(h1 - h0), 256, 0, st>>>(C, h.w_pad, h0, h1, p.w, cmin,
+                                                               p.hx_inv, p.hz_inv, x0, off,
+                                                               hk.need(nh, ws), hc.need(nh, ws));
                 JP_CHECK_LAUNCH();
             }
         }
-        const uint64_t* fk = uk;
-        const uint32_t* fc = lc;
-        int64_t nf = m;
-        if (nh > 0) {
-            const int64_t rows = x1 - x0;
-            int64_t* lr = lrow.need(rows + 1, ws);
-            int64_t* hr = hrow.need(rows + 1, ws);
-            row_bounds_kernel<<<G(rows + 1), 256, 0, st>>>(uk, m, rows, lr);
-            JP_CHECK_LAUNCH();
-            row_bounds_kernel<<<G(rows + 1), 256, 0, st>>>(hk.p, nh, rows, hr);
-            JP_CHECK_LAUNCH();
-            uint64_t* ok = mk.need(m + nh, ws);
-            uint32_t* oc = mc.need(m + nh, ws);
-            if (m > 0) {
-                merge_rows_kernel<<<G(m), 256, 0, st>>>(uk, lc, m, hk.p, hr, ok, oc);
+        ml = m > 0 ? read1(idx + m, st) : 0;
+        // both lists written to the range's output in key order
+        const int64_t nk = ml + nh;
+        if (nk > 0) {
+            Piece pc{ws.get<int32_t>(nk), ws.get<int32_t>(nk), ws.get<int32_t>(nk), nk};
+            int64_t* hr = nullptr;
+            if (nh > 0) {
+                hr = hrow.need(rows + 1, ws);
+                row_bounds_kernel<<<G(rows + 1), 256, 0, st>>>(hk.p, nh, rows, hr);
                 JP_CHECK_LAUNCH();
             }
-            merge_rows_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, uk, lr, ok, oc);
-            JP_CHECK_LAUNCH();
-            fk = ok;
-            fc = oc;
-            nf = m + nh;
-        }
-        // pairs counted at least c_min
-        if (nf > 0) {
-            uint32_t* kf = kflag.need(nf, ws);
-            uint32_t* kp = kpos.need(nf, ws);
-            keep_flag_kernel<<<G(nf), 256, 0, st>>>(fc, nf, cmin, kf);
-            JP_CHECK_LAUNCH();
-            scan_u32(kf, kp, nf, d_total, ws, st);
-            const int64_t nk = read1(d_total, st);
-            if (nk > 0) {
-                Piece pc{ws.get<int32_t>(nk), ws.get<int32_t>(nk), ws.get<int32_t>(nk), nk};
-                write_pairs_kernel<<<G(nf), 256, 0, st>>>(fk, fc, nf, kf, kp, x0, g.xval, g.zval,
-                                                          pc.x, pc.z, pc.c);
+            if (ml > 0) {
+                out_light_kernel<<<G(m), 256, 0, st>>>(uk, lc, flag, idx, m, hk.p, hr, x0, g.xval,
+                                                       g.zval, pc.x, pc.z, pc.c);
                 JP_CHECK_LAUNCH();
-                pieces.push_back(pc);
-                total += nk;
             }
+            if (nh > 0) {
+                int64_t* lr = lrow.need(rows + 1, ws);
+                row_bounds_kernel<<<G(rows + 1), 256, 0, st>>>(uk, m, rows, lr);
+                JP_CHECK_LAUNCH();
+                out_heavy_kernel<<<G(nh), 256, 0, st>>>(hk.p, hc.p, nh, uk, lr, idx, x0, g.xval,
+                                                        g.zval, pc.x, pc.z, pc.c);
+                JP_CHECK_LAUNCH();
+            }
+            pieces.push_back(pc);
+            total += nk;
         }
         out.light_pairs += m;
-        out.heavy_pairs += nh;          // heavy-only pairs; the absorbed ones are added below
         JP_CUDA_TRY(cudaEventRecord(ev.e[3], st));
         JP_CUDA_TRY(cudaEventSynchronize(ev.e[3]));
         out.ms_fill += elapsed(ev.e[0], ev.e[1]);
@@ -463,7 +478,12 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
         ++out.ranges;
         x0 = x1;
     }
-    out.heavy_pairs += (int64_t)read1(d_absorbed, st);
+    {
+        unsigned long long hv[2];
+        JP_CUDA_TRY(cudaMemcpyAsync(hv, d_absorbed, sizeof(hv), cudaMemcpyDeviceToHost, st));
+        JP_CUDA_TRY(cudaStreamSynchronize(st));
+        out.heavy_pairs = (int64_t)(hv[0] + hv[1]);   // entries taken by light pairs + the rest
+    }
     if (total >= ((int64_t)1 << 32)) throw Error{JP_EUNSUPPORTED, "2^32 or more result pairs"};
     // the pieces one after another
     int32_t* X = ws.get<int32_t>(total + 1);
