@@ -51,6 +51,13 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     lib.jp_two_path_filter.restype = ctypes.c_int
     lib.jp_two_path_filter.argtypes = [ctypes.c_void_p] * 5
     assert lib.jp_two_path_filter(None, None, None, None, None) == -1
+    lib.jp_two_path_counts.restype = ctypes.c_int
+    lib.jp_two_path_counts.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    assert lib.jp_two_path_counts(None, None, None, 1, 0, None) == -1
+    lib.jp_set_count_chunk.restype = ctypes.c_int
+    lib.jp_set_count_chunk.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    assert lib.jp_set_count_chunk(None, 1 << 20) == -1
     lib.jp_selftest_wait.restype = ctypes.c_int
     lib.jp_selftest_wait.argtypes = [ctypes.c_void_p, ctypes.c_int64]
     assert lib.jp_selftest_wait(None, 1000) == -1
