@@ -34,19 +34,46 @@ inline int GW(int64_t n) { return grid_for(n * 32, 256, 152 * 16); }   // a warp
 __global__ void entry_count_kernel(const int32_t* __restrict__ rxoff, const int32_t* __restrict__ rycol,
                                    int64_t nx, const int32_t* __restrict__ hx,
                                    const int32_t* __restrict__ hy, const int32_t* __restrict__ syoff,
-                                   const int32_t* __restrict__ sloff, int64_t* __restrict__ ecnt,
-                                   int32_t* __restrict__ rowx) {
+                                   const int32_t* __restrict__ sloff,
+                                   const int32_t* __restrict__ deg_rx, uint32_t c_min,
+                                   int64_t* __restrict__ ecnt, int32_t* __restrict__ rowx) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < nx; x += nw) {
         const bool ah = hx[x] >= 0;
+        const bool small = (uint32_t)deg_rx[x] < c_min;   // no pair of x reaches c_min
         for (int32_t k = rxoff[x] + lane; k < rxoff[x + 1]; k += 32) {
             const int32_t b = rycol[k];
             const int32_t j = ah ? hy[b] : -1;
-            ecnt[k] = (j >= 0) ? (sloff[j + 1] - sloff[j]) : (syoff[b + 1] - syoff[b]);
+            ecnt[k] = small ? 0 : (j >= 0) ? (sloff[j + 1] - sloff[j]) : (syoff[b + 1] - syoff[b]);
             rowx[k] = (int32_t)x;
         }
     }
+}
+
+// The lists col[off[r] .. off[r + 1]) restricted to the values v with deg[v] >= c_min (a pair
+// with a smaller set cannot share c_min values): flags, then positions, list and offsets.
+__global__ void size_flag_kernel(const int32_t* __restrict__ col, int64_t n,
+                                 const int32_t* __restrict__ deg, uint32_t c_min,
+                                 uint32_t* __restrict__ flag) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        flag[e] = (uint32_t)deg[col[e]] >= c_min ? 1u : 0u;
+}
+
+__global__ void size_compact_kernel(const int32_t* __restrict__ col, int64_t n,
+                                    const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                                    int32_t* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (flag[e]) out[pos[e]] = col[e];
+}
+
+__global__ void size_offsets_kernel(const int32_t* __restrict__ off, int64_t rows,
+                                    const uint32_t* __restrict__ pos, int32_t* __restrict__ out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= rows;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[r] = (int32_t)pos[off[r]];
 }
 
 // coff[x] = offset of x's first candidate (eoff at its first entry)
@@ -64,12 +91,14 @@ __global__ void cand_fill_kernel(int64_t k0, int64_t k1, int64_t x0, const int64
                                  const int32_t* __restrict__ hx, const int32_t* __restrict__ hy,
                                  const int32_t* __restrict__ syoff, const int32_t* __restrict__ szcol,
                                  const int32_t* __restrict__ sloff, const int32_t* __restrict__ slcol,
+                                 const int32_t* __restrict__ deg_rx, uint32_t c_min,
                                  uint64_t* __restrict__ keys) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t c0 = eoff[k0];
     for (int64_t k = k0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < k1; k += nw) {
         const int32_t x = rowx[k];
+        if ((uint32_t)deg_rx[x] < c_min) continue;
         const int32_t b = rycol[k];
         const int32_t j = hx[x] >= 0 ? hy[b] : -1;
         const int32_t* list;
@@ -321,14 +350,50 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
         heavy_gemm_counts(h, C, d_status, st);
     }
 
+    // with c_min > 1, S's lists (and the light-z lists of heavy y) keep only the z whose set
+    // has at least c_min values, and x with fewer than c_min values have no candidates
+    const int32_t* syoff = g.syoff;
+    const int32_t* szcol = g.szcol;
+    const int32_t* sloff = p.sloff;
+    const int32_t* slcol = p.slcol;
+    auto restrict_lists = [&](const int32_t* off, const int32_t* col, int64_t rows, int64_t n,
+                              const int32_t** off_out, const int32_t** col_out) {
+        uint32_t* flag = ws.get<uint32_t>(n + 1);
+        uint32_t* pos = ws.get<uint32_t>(n + 1);
+        int32_t* c2 = ws.get<int32_t>(n + 1);
+        int32_t* o2 = ws.get<int32_t>(rows + 1);
+        if (n > 0) {
+            size_flag_kernel<<<G(n), 256, 0, st>>>(col, n, g.deg_sz, cmin, flag);
+            JP_CHECK_LAUNCH();
+        }
+        scan_u32(flag, pos, n, pos + n, ws, st);
+        if (n > 0) {
+            size_compact_kernel<<<G(n), 256, 0, st>>>(col, n, flag, pos, c2);
+            JP_CHECK_LAUNCH();
+        }
+        size_offsets_kernel<<<G(rows + 1), 256, 0, st>>>(off, rows, pos, o2);
+        JP_CHECK_LAUNCH();
+        *off_out = o2;
+        *col_out = c2;
+    };
+    if (cmin > 1) {
+        restrict_lists(g.syoff, g.szcol, g.ny, g.ns, &syoff, &szcol);
+        if (p.v > 0) {
+            int32_t nl = 0;
+            JP_CUDA_TRY(cudaMemcpyAsync(&nl, p.sloff + p.v, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            JP_CUDA_TRY(cudaStreamSynchronize(st));
+            restrict_lists(p.sloff, p.slcol, p.v, nl, &sloff, &slcol);
+        }
+    }
+
     // light candidates per entry of R, their offsets, and per x
     const int64_t nr = g.nr;
     int64_t* ecnt = ws.get<int64_t>(nr + 1);
     int64_t* eoff = ws.get<int64_t>(nr + 1);
     int32_t* rowx = ws.get<int32_t>(nr + 1);
     int64_t* coff = ws.get<int64_t>(nx + 1);
-    entry_count_kernel<<<GW(nx), 256, 0, st>>>(g.rxoff, g.rycol, nx, p.hx, p.hy, g.syoff, p.sloff,
-                                               ecnt, rowx);
+    entry_count_kernel<<<GW(nx), 256, 0, st>>>(g.rxoff, g.rycol, nx, p.hx, p.hy, syoff, sloff,
+                                               g.deg_rx, cmin, ecnt, rowx);
     JP_CHECK_LAUNCH();
     scan_i64(ecnt, eoff, nr, eoff + nr, ws, st);
     row_offsets_kernel<<<G(nx + 1), 256, 0, st>>>(g.rxoff, nx, eoff, coff);
@@ -394,7 +459,8 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
         if (nc > 0) {
             const int64_t k0 = rxoff_host[x0], k1 = rxoff_host[x1];
             cand_fill_kernel<<<GW(k1 - k0), 256, 0, st>>>(k0, k1, x0, eoff, rowx, g.rycol, p.hx, p.hy,
-                                                          g.syoff, g.szcol, p.sloff, p.slcol, keys);
+                                                          syoff, szcol, sloff, slcol, g.deg_rx, cmin,
+                                                          keys);
             JP_CHECK_LAUNCH();
             JP_CUDA_TRY(cudaEventRecord(ev.e[1], st));
             uint64_t* sk = radix_sort_u64(keys, tmp, nc, ws, st, hist_host);
