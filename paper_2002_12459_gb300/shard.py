@@ -7,6 +7,11 @@ of S, runs the query, and the ranks' outputs, concatenated in rank order,
 are the sorted result (the paper partitions the output the same way to run
 its product in parallel, Section 6).  No data moves between ranks.
 
+The same ranges shard the set similarity join with its counts (a pair's
+count depends only on a's row; ordered by count, the ranks' lists are merged
+by count, ``merge_by_count``) and batches of set intersection requests (each
+rank answers the requests whose a lies in its range, ``shard_pairs``).
+
 The ranges are contiguous in x and balance the light join size: the weight
 of x = a is sum over its y of deg_S(y), the number of candidates the light
 expansion enumerates for a when everything is light (Section 3, the light
@@ -67,3 +72,29 @@ def shard(rx, ry, rank: int, bounds):
     lo, hi = int(bounds[rank]), int(bounds[rank + 1])
     m = (rx.astype(np.int64) >= lo) & (rx.astype(np.int64) < hi)
     return rx[m], ry[m]
+
+
+def shard_pairs(tx, tz, rank: int, bounds):
+    """Candidate pairs (a, b) of a set intersection batch whose a lies in the rank's x range.
+
+    Rank r answers them against its shard of R and all of S; the ranks' answers,
+    concatenated in rank order, are the batch's sorted answer.
+    """
+    tx = np.asarray(tx)
+    tz = np.asarray(tz)
+    lo, hi = int(bounds[rank]), int(bounds[rank + 1])
+    m = (tx.astype(np.int64) >= lo) & (tx.astype(np.int64) < hi)
+    return tx[m], tz[m]
+
+
+def merge_by_count(parts):
+    """Rank outputs (x, z, count), each by decreasing count with ties in (x, z) order, into
+    one such list: ranks hold increasing x ranges, so a stable sort of their concatenation
+    by decreasing count keeps equal counts in (x, z) order."""
+    if not parts:
+        return (np.empty(0, np.int32),) * 3
+    x = np.concatenate([np.asarray(p[0]) for p in parts])
+    z = np.concatenate([np.asarray(p[1]) for p in parts])
+    c = np.concatenate([np.asarray(p[2]) for p in parts])
+    perm = np.argsort(-c.astype(np.int64), kind="stable")
+    return x[perm], z[perm], c[perm]
