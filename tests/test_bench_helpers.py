@@ -1,0 +1,91 @@
+"""Host logic of bench.py (no GPU): the oracle sample, the roofline arithmetic, the traffic
+gate and the clock record."""
+import hashlib
+import os
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_cpu_sample_takes_a_prefix_of_x_by_candidates():
+    rx = np.array([0, 0, 1, 2, 2, 3], np.int32)
+    ry = np.array([5, 6, 5, 5, 7, 6], np.int32)
+    # deg(5) = 3, deg(6) = 2, deg(7) = 1: candidates per x 5, 3, 4, 2
+    ux, cand = bench.candidate_counts(rx, ry)
+    assert ux.tolist() == [0, 1, 2, 3] and cand.tolist() == [5, 3, 4, 2]
+    lo, hi, k, c, nx, tot = bench.cpu_sample(rx, ry, 7)
+    assert (lo, hi, k, c, nx, tot) == (0, 1, 2, 8.0, 4, 14.0)
+
+
+def _stats(**kw):
+    st = {"out_count": 1000, "u": 256, "v": 128, "w": 512, "dom_x": 10, "k": 2,
+          "light_cand": [100, 0, 0, 50, 0, 0, 25, 0], "light_x": [4, 0, 0, 2, 0, 0, 1, 0],
+          "light_deg": [8, 0, 0, 4, 0, 0, 2, 0], "light_candidates": 175,
+          "count_light_pairs": 90}
+    st.update(kw)
+    return st
+
+
+def test_gemm_roofline_is_flops_over_time_against_the_measured_rate():
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 2000.0, "fp8_tcgen05_tflops": 4800.0,
+             "int8_mma_sync_tflops": 160.0}
+    r = bench.kernel_roofline(4, _stats(), peaks, "measured", 0.5)
+    flops = 2.0 * 256 * 128 * 512
+    assert r["bound"] == "tensor" and r["achieved"] == pytest.approx(flops / 0.5e-3 / 1e12)
+    assert r["peak"] == 4800.0 and r["frac"] == pytest.approx(r["achieved"] / 4800.0)
+    assert r["frac_of_bf16_burst_x2"] == pytest.approx(r["achieved"] / 4000.0)
+
+
+def test_light_roofline_counts_its_class_bytes():
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 2000.0}
+    r = bench.kernel_roofline(9, _stats(), peaks, "measured", 1.0)   # bitmap: classes 3 and 6
+    cand, nxq = 75, (2 + 4) + (1 + 2)
+    want = 4.0 * cand + 4.0 * nxq + 4.0 * min(cand, 1000)
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(want / 1e-3 / 1e9)
+    top, per = bench.roofline(_stats(), peaks, "measured", {9: 1.0, 6: 0.2, 4: 0.1})
+    assert top["kernel"] == "light_bitmap_kernel" and set(per) == {
+        "light_bitmap_kernel", "light_warp_kernel<256>", "heavy_gemm_kernel"}
+
+
+def test_ssj_rooflines_pick_the_slowest_phase():
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 2000.0, "fp8_tcgen05_tflops": 4800.0}
+    top, per = bench.ssj_rooflines(_stats(out_count=40), peaks, {4: 0.1, 13: 0.2, 14: 3.0, 15: 0.5},
+                                   175, 90)
+    assert top["kernel"] == "radix sort + run lengths"
+    assert top["achieved"] == pytest.approx((8.0 * 175 + 12.0 * 90) / 3e-3 / 1e9)
+    assert per["cand_fill_kernel"]["achieved"] == pytest.approx(12.0 * 175 / 0.2e-3 / 1e9)
+
+
+def test_traffic_is_reported_only_for_the_captured_source():
+    m = bench.MEASURED_TRAFFIC["light_bitmap_kernel"]
+    src = open(os.path.join(bench.ROOT, m["source"]), "rb").read()
+    same = hashlib.sha1(src).hexdigest() == m["sha1"]
+    got = bench.measured_traffic("light_bitmap_kernel", m["workload"])
+    assert got == (m["bytes"] if same else None)
+    assert bench.measured_traffic("light_bitmap_kernel", "star3_2m") is None
+    assert bench.measured_traffic("place_kernel", m["workload"]) is None
+
+
+class _Proc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_record_median_under_load_and_reasons(tmp_path):
+    path = tmp_path / "clocks.csv"
+    rows = ["0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2070, 2070, 950.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1980, 2070, 880.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 345, 2070, 90.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage"]
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path, cs.fh = _Proc(), str(path), open(os.devnull, "w")
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0   # idle sample left out
+    assert rec["reasons"] == ["sw_power_cap"] and rec["samples"] == 4
