@@ -1,10 +1,12 @@
-// The batch form of the two-path query (the paper's BSI setting): a set T of
-// candidate pairs (x, z) is answered with T ∩ Q, Q(x,z) = R(x,y), S(z,y).
+// Boolean set intersection queries in batches (Section 3.3): a set T of
+// candidate pairs (x, z) is answered with T ∩ Q, Q(x,z) = R(x,y), S(z,y), i.e.
+// the query Q_batch(x,z) = R(x,y), S(z,y), T(x,z).
 //
 // Only the x values of T can start an answer and only its z values can end
 // one, so R is first reduced to the tuples whose x occurs in T and S to those
-// whose z occurs in T (semi-joins); Q of the reduced relations holds every
-// answer.  Its sorted output is then searched for each pair of T.
+// whose z occurs in T (semi-joins, as the section's experiments do before
+// running Algorithm 1); Q of the reduced relations holds every answer.  Its
+// sorted output is then searched for each pair of T.
 #include "jp_internal.cuh"
 
 namespace jp {
