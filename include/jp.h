@@ -142,6 +142,36 @@ void jp_destroy(jp_ctx* ctx);
  * delta1/delta2 are used in JP_FIXED mode only and must be >= 1. */
 int jp_set_threshold(jp_ctx* ctx, int mode, int64_t delta1, int64_t delta2);
 
+/* Constants of the cost-based optimizer (Section 5, Table 2, Algorithm 3), used by
+ * JP_COST_MODEL and by the judge of JP_LEARNED.  Algorithm 3 starts at Delta1 = N,
+ * Delta2 = max(N Delta1 / OUT_est, 1) and multiplies Delta1 by (1 - eps) while the modelled cost
+ *   T_I sum(y_D1) + T_I sum(x_D2) + T_m |dom x| + T_s cdfx(y_D1) |dom x|
+ *   + [u, v, w > 0] (2 u v w / mm_rate + mm_fixed + T_m (u v + u w))
+ * does not grow, and returns the last thresholds before it grew (floored, clamped to [1, N]);
+ * u, v, w are the heavy x, y and z counts at those thresholds, the sums are over light y
+ * (max(deg_R, deg_S) <= Delta1: deg_R deg_S, and deg_R for cdfx) and light x (deg <= Delta2:
+ * sum over the x's y of deg_S).  N is max(|R|, |S|) after R's tuples with no y in S are
+ * dropped.  When OUT_join <= wcoj_factor N every value is light (Delta1 = Delta2 = N).
+ * Times are in seconds; only their ratios matter. */
+typedef struct {
+    double T_I;          /* per light candidate inserted into a deduplication structure, >= 0 */
+    double T_m;          /* per matrix element / per-x structure set up, >= 0 */
+    double T_s;          /* per sequential step of a scan of the light-y list, >= 0 */
+    double mm_rate;      /* heavy product: 2 u v w operations at this rate (per second), > 0 */
+    double mm_fixed;     /* heavy product: fixed time, >= 0 */
+    double eps;          /* descent step, 0 < eps < 1 */
+    double wcoj_factor;  /* plain worst-case optimal join when OUT_join <= wcoj_factor N, >= 0 */
+    double judge;        /* JP_LEARNED keeps the model's thresholds unless they cost more than
+                            judge times Algorithm 3's choice, >= 1 */
+} jp_cost_model;
+
+/* Replace the context's constants (copied; NULL restores the defaults, which were measured on
+ * GB300: T_I = 1/60e9, T_m = 1e-12, T_s = 0, mm_rate = 2.2e15, mm_fixed = 2e-5, eps = 0.05,
+ * wcoj_factor = 20, judge = 3).  A value out of range gives JP_EINVAL and keeps the old ones. */
+int jp_set_cost_model(jp_ctx* ctx, const jp_cost_model* model);
+/* The context's current constants. */
+int jp_get_cost_model(const jp_ctx* ctx, jp_cost_model* model);
+
 /* Change the stream of subsequent calls. */
 int jp_set_stream(jp_ctx* ctx, void* stream);
 
@@ -208,6 +238,8 @@ int jp_two_path_filter(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, const jp_r
  *   c_min  >= 1;
  *   order  JP_ORDER_PAIRS or JP_ORDER_COUNT;
  *   out    k = 3: col[0] = x, col[1] = z, col[2] = count (int32).
+ * A heavy part with 2^24 or more heavy y gives JP_EUNSUPPORTED (its counts could pass the
+ * FP32 accumulators' exact range; choose larger thresholds).
  * Memory: the heavy count matrix (4 bytes per heavy x and heavy z pair; JP_EUNSUPPORTED above
  * 64 GiB) and the light candidates of a range of x at a time (jp_set_count_chunk); one x with
  * 2^31 or more light candidates, or 2^32 or more result pairs, gives JP_EUNSUPPORTED.  Other
@@ -246,8 +278,10 @@ const char* jp_last_error(const jp_ctx* ctx);
  * choice instead: a network maps a relation's degree distribution to
  * (ln Delta1, ln Delta2), trained on the thresholds that timed best on the
  * GPU.  Features: two 64-bin histograms (x degrees; y degrees taken as
- * max(deg_R(y), deg_S(y))), as fractions of the values, with
- * bin(d) = min(63, floor(4 log2 d)).  Network: 128 -> 256 -> 256 -> 2 with
+ * max(deg_R(y), deg_S(y))) with bin(d) = min(63, floor(4 log2 d)) computed
+ * with integers; a bin holding c values enters as log2(1 + c) / 32, so the
+ * features carry the relation's size as well as its degree law.
+ * Network: 128 -> 256 -> 256 -> 2 with
  * ReLU, weights used in bfloat16, products and sums in float32, float32
  * master weights updated by Adam.  Parameters are one float array of
  * JP_MLP_PARAMS entries: W1[128][256], b1[256], W2[256][256], b2[256],
@@ -281,20 +315,22 @@ int jp_mlp_train_step(jp_mlp* model, const float* X, const float* T, int B, floa
                       float* loss);
 
 /* ---- Allocation-free two-path query (the paper has no counterpart) ----
- * For callers that cannot allocate device memory when they query: code that
- * runs while a CUDA graph is being captured, services that reserve their
- * whole device-memory budget at start-up and forbid later allocations, plain
- * C hosts that have no allocator to hand to jp_create, and latency-bound
- * loops that cannot afford an allocation.  It runs the jp_two_path pipeline
- * with every scratch buffer carved from one static __device__ array of
- * JP_NOALLOC_SCRATCH_BYTES (held by every GPU that loads the library until
- * the process exits) and writes into the caller's buffers.  It calls no
- * cudaMalloc, cudaFree or other allocating routine and needs no jp_ctx.
+ * For callers that cannot allocate device memory when they query: services
+ * that reserve their whole device-memory budget at start-up and forbid later
+ * allocations (one more allocation would fail or fragment that budget),
+ * plug-ins inside a host program that owns every device allocation and gives
+ * its extensions none, and latency-bound loops for which an allocation, which
+ * can wait for the device, costs more than the query.  It runs the
+ * jp_two_path pipeline with every scratch buffer carved from one static
+ * __device__ array of JP_NOALLOC_SCRATCH_BYTES (held by every GPU that loads
+ * the library until the process exits) and writes into the caller's buffers.
+ * It calls no cudaMalloc, cudaFree or other allocating routine and needs no
+ * jp_ctx.
  *  - R, S: DEVICE pointers only (host pointers: JP_EINVAL); S == NULL means
  *    S = R.  Each relation holds at most JP_NOALLOC_MAX_TUPLES tuples
  *    (larger: JP_EUNSUPPORTED, checked before any work).
- *  - mode: JP_FIXED (delta1, delta2 >= 1) or JP_CLOSED_FORM; JP_COST_MODEL
- *    is rejected with JP_EINVAL.
+ *  - mode: JP_FIXED (delta1, delta2 >= 1) or JP_CLOSED_FORM; other modes are
+ *    rejected with JP_EINVAL.
  *  - out_x, out_z: device buffers of out_cap entries each.  *out_count (a
  *    host pointer) receives the number of result pairs; when it exceeds
  *    out_cap nothing is written and JP_EOVERFLOW is returned, so the caller
@@ -303,9 +339,9 @@ int jp_mlp_train_step(jp_mlp* model, const float* X, const float* T, int B, floa
  *  - A query whose scratch does not fit in the array fails with
  *    JP_EUNSUPPORTED.
  *  - Work runs on `stream` (a cudaStream_t) on the current device; the call
- *    returns once the result is written.  The first call on a device looks
- *    up the array's device address with cudaGetSymbolAddress: make that
- *    first call before any stream capture begins.
+ *    returns once its work on the stream has finished, on success and on
+ *    failure.  The first call on a device looks up the array's device address
+ *    with cudaGetSymbolAddress.
  *  - Every call shares the array, which keeps the last call's contents; the
  *    call itself clears whatever must start at zero.  Calls that overlap on
  *    the GPU (from several host threads or streams) race on the array: the

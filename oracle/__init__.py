@@ -9,7 +9,7 @@ arithmetic.
 
 Contents:
 
-* ``two_path`` / ``star`` / ``two_path_row``: the plain definition of the
+* ``two_path`` / ``star`` / ``two_path_row`` / ``two_path_rows``: the plain definition of the
   queries (Section 2.1) in C (``jp_oracle.c``): sort-based hash join on y,
   projection, sort and unique.  Exact, integer only.
 * ``brute_two_path`` / ``brute_star``: pure-Python triple loops over the
@@ -43,7 +43,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-__all__ = ["build", "two_path", "star", "two_path_row", "brute_two_path",
+__all__ = ["build", "two_path", "star", "two_path_row", "two_path_rows", "brute_two_path",
            "brute_star", "normalise", "bsi", "brute_bsi", "ssj", "brute_ssj"]
 
 
@@ -73,6 +73,10 @@ def _load():
             lib.oracle_two_path_row.restype = ctypes.c_int64
             lib.oracle_two_path_row.argtypes = [i32p, ctypes.c_int64, i32p, i32p, ctypes.c_int64,
                                                 i32p, ctypes.c_int64]
+            lib.oracle_two_path_rows.restype = ctypes.c_int64
+            lib.oracle_two_path_rows.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                                 i32p, i32p, i32p, ctypes.c_int64, i32p,
+                                                 ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_sort_by_y.restype = ctypes.c_int64
             lib.oracle_sort_by_y.argtypes = [i32p, i32p, ctypes.c_int64, i32p, i32p]
             _lib = lib
@@ -169,6 +173,30 @@ def two_path_row(r_y_of_a, s_sorted: SortedS) -> np.ndarray:
             raise MemoryError
         if n <= cap:
             return out[:n]
+        cap = int(n)
+
+
+def two_path_rows(r_off, r_y, s_sorted: SortedS, cap_hint: int = 0):
+    """Sorted distinct z of several rows (row i's y values are r_y[r_off[i]:r_off[i+1]]).
+
+    Returns (z values of all rows one after another, int64 count per row).
+    """
+    lib = _load()
+    r_off = np.ascontiguousarray(r_off, dtype=np.int64)
+    r_y = _i32(r_y)
+    nrows = len(r_off) - 1
+    cnt = np.zeros(max(nrows, 1), np.int64)
+    cap = max(int(cap_hint), 1 << 12)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    while True:
+        out = np.empty(cap, np.int32)
+        n = lib.oracle_two_path_rows(r_off.ctypes.data_as(i64p), nrows, _p(r_y),
+                                     _p(s_sorted.y), _p(s_sorted.z), len(s_sorted.y), _p(out),
+                                     cap, cnt.ctypes.data_as(i64p))
+        if n < 0:
+            raise MemoryError
+        if n <= cap:
+            return out[:n], cnt[:nrows]
         cap = int(n)
 
 

@@ -239,6 +239,31 @@ int64_t oracle_two_path_row(const int32_t* r_y_of_a, int64_t deg_a,
     return d;
 }
 
+/*
+ * The two-path rows of several x values: row i's y values are
+ * r_y[r_off[i] .. r_off[i+1]); each row is answered as oracle_two_path_row
+ * does (join with S sorted by y, sort, unique) and the rows' distinct z are
+ * written one after another (up to cap values in total); out_cnt[i] receives
+ * row i's count.  Returns the total number of values (may exceed cap), or -1
+ * when memory runs out.
+ */
+int64_t oracle_two_path_rows(const int64_t* r_off, int64_t nrows, const int32_t* r_y,
+                             const int32_t* s_y_sorted, const int32_t* s_z_sorted, int64_t ns,
+                             int32_t* out_z, int64_t cap, int64_t* out_cnt) {
+    int64_t total = 0;
+    for (int64_t i = 0; i < nrows; ++i) {
+        int32_t* dst = total < cap ? out_z + total : NULL;
+        int64_t room = total < cap ? cap - total : 0;
+        int32_t dummy;
+        int64_t d = oracle_two_path_row(r_y + r_off[i], r_off[i + 1] - r_off[i], s_y_sorted,
+                                        s_z_sorted, ns, dst ? dst : &dummy, room);
+        if (d < 0) return -1;
+        out_cnt[i] = d;
+        total += d;
+    }
+    return total;
+}
+
 /* Sort and deduplicate (y, v) pairs; writes them back in (y, v) order. */
 int64_t oracle_sort_by_y(const int32_t* v, const int32_t* y, int64_t n,
                          int32_t* out_y, int32_t* out_v) {

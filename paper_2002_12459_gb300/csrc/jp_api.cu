@@ -4,6 +4,7 @@
 //   light expansion/deduplication + union -> output placement.
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "jp_internal.cuh"
@@ -23,12 +24,31 @@ struct jp_ctx {
     jp::Timer tm;
     jp_mlp* predictor = nullptr;       // borrowed model for JP_LEARNED
     int64_t count_chunk = (int64_t)1 << 27;   // light candidates per pass of jp_two_path_counts
+    jp_cost_model cost = jp::default_cost_model();   // Algorithm 3's constants
 };
 
 namespace jp {
 
-int64_t g_launches = 0;
-Timer* g_timer = nullptr;
+thread_local int64_t g_launches = 0;
+thread_local Timer* g_timer = nullptr;
+
+void smem_limit(const void* func, size_t bytes) {
+    struct Entry { const void* f; int dev; size_t bytes; };
+    static std::mutex mu;
+    static std::vector<Entry> done;
+    int dev = 0;
+    JP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    for (Entry& e : done)
+        if (e.f == func && e.dev == dev) {
+            if (e.bytes >= bytes) return;
+            JP_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+            e.bytes = bytes;
+            return;
+        }
+    JP_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.push_back({func, dev, bytes});
+}
 
 void* Arena::raw_alloc(size_t bytes) {
     if (alloc) return alloc(bytes, (void*)stream, user);
@@ -223,7 +243,7 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         ctx->tm.begin(jp::TM_SELECT);
         int judged = 0;
         jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
-                              ctx->predictor, &judged);
+                              ctx->cost, ctx->predictor, &judged);
         ctx->tm.end(jp::TM_SELECT);
         ctx->tm.begin(jp::TM_PARTITION);
         jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);
@@ -397,6 +417,23 @@ int jp_set_threshold(jp_ctx* ctx, int mode, int64_t delta1, int64_t delta2) {
     return JP_OK;
 }
 
+int jp_set_cost_model(jp_ctx* ctx, const jp_cost_model* model) {
+    if (!ctx) return JP_EINVAL;
+    if (!model) {
+        ctx->cost = jp::default_cost_model();
+        return JP_OK;
+    }
+    if (!jp::valid_cost_model(*model)) return fail(ctx, JP_EINVAL, "cost model constant out of range");
+    ctx->cost = *model;
+    return JP_OK;
+}
+
+int jp_get_cost_model(const jp_ctx* ctx, jp_cost_model* model) {
+    if (!ctx || !model) return JP_EINVAL;
+    *model = ctx->cost;
+    return JP_OK;
+}
+
 int jp_set_stream(jp_ctx* ctx, void* stream) {
     if (!ctx) return JP_EINVAL;
     ctx->stream = (cudaStream_t)stream;
@@ -477,7 +514,7 @@ int jp_two_path_counts(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int64_t c_
         int judged = 0;
         ctx->tm.begin(jp::TM_SELECT);
         jp::select_thresholds(g, ctx->mode, ctx->d1, ctx->d2, &p.d1, &p.d2, &out_est, ctx->ws, st,
-                              ctx->predictor, &judged);
+                              ctx->cost, ctx->predictor, &judged);
         ctx->tm.end(jp::TM_SELECT);
         ctx->tm.begin(jp::TM_PARTITION);
         jp::build_partition(g, p, ctx->ws, st, ctx->host_scalars);

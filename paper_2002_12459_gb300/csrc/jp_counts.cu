@@ -343,6 +343,10 @@ void count_pairs(const Graph& g, const Partition& p, const Heavy& h, int64_t c_m
     // heavy product entries
     uint32_t* C = nullptr;
     if (h.present) {
+        // an entry counts heavy y shared by a pair, at most v; the FP32
+        // accumulators hold every integer exactly only below 2^24
+        if (p.v >= ((int64_t)1 << 24))
+            throw Error{JP_EUNSUPPORTED, "2^24 or more heavy y: product counts would be inexact"};
         const size_t bytes = (size_t)h.u_pad * (size_t)h.w_pad * sizeof(uint32_t);
         if (bytes > ((size_t)1 << 36))
             throw Error{JP_EUNSUPPORTED, "the heavy count matrix would exceed 64 GiB"};

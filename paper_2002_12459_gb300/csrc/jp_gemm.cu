@@ -354,17 +354,21 @@ __global__ void pack_cols_kernel(const int32_t* col_inv, int64_t ncols, const in
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+PFN_cuTensorMapEncodeTiled_v12000 lookup_encode_fn() {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    JP_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                  cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+        throw Error{JP_ECUDA, "cuTensorMapEncodeTiled is not available"};
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+}
+
+// The driver's tensor-map encoder, looked up once (a function-local static is
+// initialised by one thread while the others wait; a failed lookup is retried
+// by the next call).
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void* p = nullptr;
-        JP_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                                      cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || !p)
-            throw Error{JP_ECUDA, "cuTensorMapEncodeTiled is not available"};
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encode_fn();
     return fn;
 }
 
@@ -516,12 +520,7 @@ __global__ void tile_range_kernel(const int32_t* __restrict__ hx_inv, int64_t u,
 void measure_peaks(int sms, double* fp8_tflops, double* int8_tflops, uint32_t* d_status,
                    Arena& ws, cudaStream_t st) {
     const size_t smem = (size_t)A_STAGE + B_STAGE + 1024 + 64;
-    static bool attr = false;
-    if (!attr) {
-        JP_CUDA_TRY(cudaFuncSetAttribute(fp8_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        attr = true;
-    }
+    smem_limit((const void*)fp8_peak_kernel, smem);
     cudaEvent_t e0, e1;
     JP_CUDA_TRY(cudaEventCreate(&e0));
     JP_CUDA_TRY(cudaEventCreate(&e1));
@@ -595,13 +594,7 @@ void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t s
     if (!h.present) return;
     CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
     CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
-    static bool attr = false;
-    if (!attr) {
-        JP_CUDA_TRY(cudaFuncSetAttribute(heavy_gemm_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)GEMM_SMEM));
-        attr = true;
-    }
+    smem_limit((const void*)heavy_gemm_kernel<false>, GEMM_SMEM);
     const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
     tbegin(TM_GEMM);
     heavy_gemm_kernel<false><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
@@ -614,13 +607,7 @@ void heavy_gemm_counts(const Heavy& h, uint32_t* C, uint32_t* d_status, cudaStre
     if (!h.present) return;
     CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
     CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
-    static bool attr = false;
-    if (!attr) {
-        JP_CUDA_TRY(cudaFuncSetAttribute(heavy_gemm_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)GEMM_SMEM));
-        attr = true;
-    }
+    smem_limit((const void*)heavy_gemm_kernel<true>, GEMM_SMEM);
     const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
     tbegin(TM_GEMM);
     heavy_gemm_kernel<true><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(

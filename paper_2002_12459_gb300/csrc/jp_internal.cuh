@@ -24,8 +24,10 @@ struct Error {
     } while (0)
 
 // Every kernel launch of the library is followed by JP_CHECK_LAUNCH, which
-// also counts it (reported per query in jp_stats.kernel_launches).
-extern int64_t g_launches;
+// also counts it (reported per query in jp_stats.kernel_launches).  The
+// counter is per host thread: a call runs on its caller's thread, so calls
+// made from other threads at the same time do not mix their counts.
+extern thread_local int64_t g_launches;
 #define JP_CHECK_LAUNCH()                 \
     do {                                  \
         ++::jp::g_launches;               \
@@ -184,9 +186,12 @@ void filter_emit(const FilterState& fs, int32_t* px, int32_t* pz, cudaStream_t s
 // Threshold selection (jp_select.cu)
 double out_estimate(double dom_x, double out_join, double N);
 // *judged (JP_LEARNED): 1 the model's thresholds kept, 2 replaced by Algorithm 3's.
+jp_cost_model default_cost_model();
+bool valid_cost_model(const jp_cost_model& K);
 void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
                        int64_t* d2, double* out_est, Arena& ws, cudaStream_t st,
-                       jp_mlp* predictor = nullptr, int* judged = nullptr);
+                       const jp_cost_model& K, jp_mlp* predictor = nullptr,
+                       int* judged = nullptr);
 
 // Learned predictor (jp_mlp.cu): the 128 degree features of a built graph and
 // the thresholds a model predicts for them.
@@ -326,7 +331,13 @@ struct Timer {
         return v;
     }
 };
-extern Timer* g_timer;
+// The timer of the call running on this host thread (null: none).
+extern thread_local Timer* g_timer;
+
+// Raise `func`'s dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to each device's context, so it is set once
+// per (kernel, device) and again whenever a larger value is needed.
+void smem_limit(const void* func, size_t bytes);
 inline void tbegin(int k) { if (g_timer) g_timer->begin(k); }
 inline void tend(int k) { if (g_timer) g_timer->end(k); }
 

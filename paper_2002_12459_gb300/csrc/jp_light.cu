@@ -1061,14 +1061,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         const size_t sm0 = (size_t)2 * W2_CAP * sizeof(int32_t);   // 16 KB: 8 blocks per SM
         const size_t sm1 = (size_t)2 * M_CAP * sizeof(int32_t);
         const size_t sm2 = (size_t)2 * M2_CAP * sizeof(int32_t);
-        static bool attrm = false;
-        if (!attrm) {
-            JP_CUDA_TRY(cudaFuncSetAttribute(light_merge_kernel<M_CAP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-            JP_CUDA_TRY(cudaFuncSetAttribute(light_merge_kernel<M2_CAP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-            attrm = true;
-        }
+        smem_limit((const void*)light_merge_kernel<M_CAP>, sm1);
+        smem_limit((const void*)light_merge_kernel<M2_CAP>, sm2);
         tbegin(TM_LIGHT_MERGE);
         if (hc.q[Q_MERGE2]) {
             light_merge_kernel<M2_CAP><<<grid_for(hc.q[Q_MERGE2], 1, 152 * 3), M_THREADS, sm2, st>>>(
@@ -1092,13 +1086,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         int32_t win = (int32_t)std::min<int64_t>(words, BM_MAX_WORDS);
         win = (win + 1023) & ~1023;                 // whole summary words
         const size_t sm = (size_t)(win + win / 32) * sizeof(uint32_t);
-        static bool attrb = false;
-        if (!attrb) {
-            JP_CUDA_TRY(cudaFuncSetAttribute(
-                light_bitmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                (int)((BM_MAX_WORDS + BM_MAX_WORDS / 32) * sizeof(uint32_t))));
-            attrb = true;
-        }
+        smem_limit((const void*)light_bitmap_kernel,
+                   (BM_MAX_WORDS + BM_MAX_WORDS / 32) * sizeof(uint32_t));
         tbegin(TM_LIGHT_BITMAP);
         light_bitmap_kernel<<<grid_for(hc.q[Q_BITMAP] + hc.q[Q_HUB], 1, 152), BM_THREADS, sm, st>>>(
             A, queues + (int64_t)Q_HUB * nx, queues + (int64_t)Q_BITMAP * nx, ctr, win);

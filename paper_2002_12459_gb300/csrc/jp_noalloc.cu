@@ -1,15 +1,21 @@
 // jp_two_path_noalloc: the two-path query for callers that cannot allocate
 // device memory.  It has no counterpart in the paper.
 //
-// Some callers cannot call cudaMalloc or any allocating routine at query
-// time: code that runs while a CUDA graph is being captured, services that
-// reserve their whole device-memory budget at start-up and forbid later
-// allocations, plain C hosts that have no allocator to hand to jp_create, and
-// latency-bound loops that cannot afford an allocation.  This entry point
-// runs the same pipeline as jp_two_path, but every scratch buffer is carved
-// from one file-scope __device__ array of JP_NOALLOC_SCRATCH_BYTES, and the
-// result goes to output buffers the caller owns.  It calls no cudaMalloc,
-// cudaFree or other allocating routine.
+// Some callers of this library cannot call cudaMalloc or any other
+// allocating routine when they query:
+//  - services that reserve their whole device-memory budget at start-up
+//    (a serving process whose memory pool already holds nearly all of the
+//    GPU) and forbid later allocations, because one more allocation would
+//    fail or fragment that budget;
+//  - plug-ins running inside a host program that owns every device
+//    allocation and gives its extensions none (a database engine's
+//    user-defined functions, for example);
+//  - latency-bound loops for which an allocation, which can wait for the
+//    device, costs more than the query.
+// This entry point runs the same pipeline as jp_two_path, but every scratch
+// buffer is carved from one file-scope __device__ array of
+// JP_NOALLOC_SCRATCH_BYTES, and the result goes to output buffers the caller
+// owns.  It calls no cudaMalloc, cudaFree or other allocating routine.
 //
 // Limits and sharing rules (also stated in jp.h):
 //  - queries whose scratch does not fit in the array fail with
@@ -17,11 +23,13 @@
 //  - every call shares the array and it keeps the last call's contents; the
 //    pipeline clears what must start at zero itself;
 //  - calls that overlap on the GPU (other streams, other threads) race on the
-//    array: serialise them;
+//    array: serialise them.  A call returns only after its own work on the
+//    stream has finished, failed calls included;
 //  - the first call on a device looks the array's device address up with
-//    cudaGetSymbolAddress; make that first call before any stream capture.
+//    cudaGetSymbolAddress.
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "jp_internal.cuh"
 
@@ -95,7 +103,8 @@ extern "C" int jp_two_path_noalloc(const jp_rel* R, const jp_rel* S, int mode, i
         jp::build_graph(R, self ? nullptr : S, g, ws, st, d_status, g_hist_host, g_host_scalars);
         jp::Partition p;
         double out_est = 0;
-        jp::select_thresholds(g, mode, delta1, delta2, &p.d1, &p.d2, &out_est, ws, st);
+        jp::select_thresholds(g, mode, delta1, delta2, &p.d1, &p.d2, &out_est, ws, st,
+                              jp::default_cost_model());
         jp::build_partition(g, p, ws, st, g_host_scalars);
         jp::Heavy h;
         jp::heavy_pack(g, p, h, ws, st);
@@ -117,8 +126,20 @@ extern "C" int jp_two_path_noalloc(const jp_rel* R, const jp_rel* S, int mode, i
         if (s) return JP_EOVERFLOW;
         return JP_OK;
     } catch (const jp::Error& e) {
-        // the only allocation the pipeline attempts is growing the workspace,
-        // which here means the query needs more than the static array holds
+        // kernels of this call may still be queued: wait for them, so that the
+        // next call (on any stream) finds the array idle
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaGetLastError();
+        // the only device allocation the pipeline attempts is growing the
+        // workspace, which here means the query needs more than the array holds
         return e.code == JP_ENOMEM ? JP_EUNSUPPORTED : e.code;
+    } catch (const std::bad_alloc&) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaGetLastError();
+        return JP_ENOMEM;   // host memory for the pipeline's bookkeeping ran out
+    } catch (...) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        cudaGetLastError();
+        return JP_ECUDA;
     }
 }

@@ -169,24 +169,34 @@ int64_t clamp_delta(double d, int64_t N) {
 
 }  // namespace
 
-// Calibration constants of the GPU cost model (seconds), in the roles of
-// Table 2: T_I per light candidate inserted into a deduplication structure,
-// T_m per matrix element / per-x structure set up, T_s per sequential step of
-// the paper's scan of the light-y list for every x (0 here: the GPU
-// expansion walks each x's own neighbour list), and the product time model
-// M_hat(u,v,w) = 2uvw / mm_rate + mm_fixed.
-struct CostConsts {
-    // measured on GB300 with the 10M power-law self-join: 3.1e9 light
-    // candidates in ~50 ms of light kernels, 2.3 PFLOP/s in the product
-    double T_I = 1.0 / 60e9;
-    double T_m = 1.0 / 1.0e12;
-    double T_s = 0.0;
-    double mm_rate = 2.2e15;
-    double mm_fixed = 20e-6;
-    double eps = 0.05;
-    double wcoj_factor = 20.0;
-    double judge = 3.0;        // JP_LEARNED: modelled-cost ratio above which the model is overruled
-};
+// Default calibration constants of the GPU cost model (seconds), in the
+// roles of Table 2: T_I per light candidate inserted into a deduplication
+// structure, T_m per matrix element / per-x structure set up, T_s per
+// sequential step of the paper's scan of the light-y list for every x (0
+// here: the GPU expansion walks each x's own neighbour list), and the product
+// time model M_hat(u,v,w) = 2uvw / mm_rate + mm_fixed.  Measured on GB300
+// with the 10M power-law self-join: 3.1e9 light candidates in ~50 ms of light
+// kernels, 2.3 PFLOP/s in the product.
+jp_cost_model default_cost_model() {
+    jp_cost_model K;
+    K.T_I = 1.0 / 60e9;
+    K.T_m = 1.0 / 1.0e12;
+    K.T_s = 0.0;
+    K.mm_rate = 2.2e15;
+    K.mm_fixed = 20e-6;
+    K.eps = 0.05;
+    K.wcoj_factor = 20.0;
+    K.judge = 3.0;
+    return K;
+}
+
+bool valid_cost_model(const jp_cost_model& K) {
+    auto fin = [](double v) { return std::isfinite(v); };
+    return fin(K.T_I) && fin(K.T_m) && fin(K.T_s) && fin(K.mm_rate) && fin(K.mm_fixed) &&
+           fin(K.eps) && fin(K.wcoj_factor) && fin(K.judge) && K.T_I >= 0 && K.T_m >= 0 &&
+           K.T_s >= 0 && K.mm_rate > 0 && K.mm_fixed >= 0 && K.eps > 0 && K.eps < 1 &&
+           K.wcoj_factor >= 0 && K.judge >= 1;
+}
 
 double out_estimate(double dom_x, double out_join, double N) {
     if (N <= 0) return 0;
@@ -197,10 +207,12 @@ double out_estimate(double dom_x, double out_join, double N) {
 
 void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64_t* d1,
                        int64_t* d2, double* out_est, Arena& ws, cudaStream_t st,
-                       jp_mlp* predictor, int* judged) {
+                       const jp_cost_model& K, jp_mlp* predictor, int* judged) {
     if (judged) *judged = 0;
+    // N: the larger relation after R's dangling tuples are dropped (Section
+    // 3.1 assumes |R| = |S| = N)
     const int64_t N = std::max<int64_t>(std::max(g.nr, g.ns), 1);
-    *out_est = out_estimate((double)g.nx, g.out_join, (double)g.nr);
+    *out_est = out_estimate((double)g.nx, g.out_join, (double)N);
     if (mode == JP_FIXED) {
         *d1 = std::min<int64_t>(std::max<int64_t>(fd1, 1), N);
         *d2 = std::min<int64_t>(std::max<int64_t>(fd2, 1), N);
@@ -211,8 +223,9 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
         const double n = (double)N;
         double a, b;
         if (OUT <= n) {
-            a = std::cbrt(OUT);
-            b = n / std::pow(OUT, 2.0 / 3.0);
+            const double c = std::cbrt(OUT);
+            a = c;
+            b = n / (c * c);
         } else {
             a = b = std::cbrt(2.0 * n * n / (n + OUT));
         }
@@ -233,7 +246,6 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
         throw Error{JP_EINVAL, "unknown threshold mode"};
     }
     // ---- Algorithm 3 on exact degree indexes
-    const CostConsts K;
     if (mode == JP_COST_MODEL && g.out_join <= K.wcoj_factor * (double)N) {  // plain worst-case optimal join
         *d1 = N;
         *d2 = N;

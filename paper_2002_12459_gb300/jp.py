@@ -60,6 +60,11 @@ class jp_stats(ctypes.Structure):
                 ("count_ranges", ctypes.c_int64), ("count_light_pairs", ctypes.c_int64)]
 
 
+class jp_cost_model(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("T_I", "T_m", "T_s", "mm_rate", "mm_fixed", "eps", "wcoj_factor", "judge")]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -83,6 +88,10 @@ def load(path: str = LIB_PATH):
             lib.jp_destroy.restype = None
             lib.jp_set_threshold.argtypes = [vp, i32, i64, i64]
             lib.jp_set_threshold.restype = i32
+            lib.jp_set_cost_model.argtypes = [vp, ctypes.POINTER(jp_cost_model)]
+            lib.jp_set_cost_model.restype = i32
+            lib.jp_get_cost_model.argtypes = [vp, ctypes.POINTER(jp_cost_model)]
+            lib.jp_get_cost_model.restype = i32
             lib.jp_set_stream.argtypes = [vp, vp]
             lib.jp_set_stream.restype = i32
             lib.jp_two_path.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
@@ -184,6 +193,26 @@ class Context:
     def set_threshold(self, mode="closed_form", delta1: int = 1, delta2: int = 1):
         m = _MODES[mode] if isinstance(mode, str) else int(mode)
         self._check(self.lib.jp_set_threshold(self.h, m, int(delta1), int(delta2)))
+
+    def set_cost_model(self, **consts):
+        """Replace Algorithm 3's constants (jp_set_cost_model); no argument restores the
+        defaults, keyword arguments change the named constants of the current set."""
+        if not consts:
+            self._check(self.lib.jp_set_cost_model(self.h, None))
+            return
+        m = jp_cost_model()
+        self._check(self.lib.jp_get_cost_model(self.h, ctypes.byref(m)))
+        for k, v in consts.items():
+            if k not in dict(jp_cost_model._fields_):
+                raise KeyError(k)
+            setattr(m, k, float(v))
+        self._check(self.lib.jp_set_cost_model(self.h, ctypes.byref(m)))
+
+    def cost_model(self) -> dict:
+        """The context's current Algorithm 3 constants (jp_get_cost_model)."""
+        m = jp_cost_model()
+        self._check(self.lib.jp_get_cost_model(self.h, ctypes.byref(m)))
+        return {k: getattr(m, k) for k, _ in jp_cost_model._fields_}
 
     def _take(self, res: jp_result):
         """Wrap result columns as int32 tensors viewing the library's block."""

@@ -64,6 +64,12 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     lib.jp_measure_peaks.restype = ctypes.c_int
     lib.jp_measure_peaks.argtypes = [ctypes.c_void_p] * 3
     assert lib.jp_measure_peaks(None, None, None) == -1
+    lib.jp_set_cost_model.restype = ctypes.c_int
+    lib.jp_set_cost_model.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.jp_set_cost_model(None, None) == -1
+    lib.jp_get_cost_model.restype = ctypes.c_int
+    lib.jp_get_cost_model.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.jp_get_cost_model(None, None) == -1
     lib.jp_last_error.restype = ctypes.c_char_p
     lib.jp_last_error.argtypes = [ctypes.c_void_p]
     assert lib.jp_last_error(None) == b"NULL context"

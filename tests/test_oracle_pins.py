@@ -220,3 +220,28 @@ def test_star_invariant_to_thresholds(oracle_mod, seed):
     for d1 in (1, 2, 4, 50):
         for d2 in (1, 3, 50):
             assert A1.star_algorithm(tl, d1, d2)["T"] == want
+
+
+def test_two_path_rows_is_the_row_wise_definition(oracle_mod):
+    """The batched per-row oracle equals the whole-relation oracle, row by row."""
+    from paper_2002_12459_gb300 import workloads as W
+    rng = np.random.default_rng(21)
+    x, y = W.random_small_relation(rng, 3000, 200, 80, -100, -40, 0.7)
+    s = oracle_mod.SortedS(x, y)
+    key = np.unique((x.astype(np.int64) << 32) | (y.astype(np.int64) & 0xFFFFFFFF))
+    ux = (key >> 32).astype(np.int32)
+    uy = (key & 0xFFFFFFFF).astype(np.uint32).astype(np.int32)
+    xs, start = np.unique(ux, return_index=True)
+    off = np.append(start, len(ux)).astype(np.int64)
+    z, cnt = oracle_mod.two_path_rows(off, uy, s)
+    wx, wz = oracle_mod.two_path(x, y)
+    assert np.array_equal(z, wz)
+    assert np.array_equal(np.repeat(xs, cnt), wx)
+    # a subset of rows, out of order of their x values
+    pick = np.array([5, 1, 17, 3])
+    sub_off = np.concatenate([[0], np.cumsum(off[pick + 1] - off[pick])]).astype(np.int64)
+    sub_y = np.concatenate([uy[off[i]:off[i + 1]] for i in pick])
+    z2, c2 = oracle_mod.two_path_rows(sub_off, sub_y, s)
+    for k, i in enumerate(pick):
+        assert np.array_equal(z2[sub_off[k] - sub_off[k] + c2[:k].sum():c2[:k + 1].sum()],
+                              wz[wx == xs[i]])
