@@ -45,8 +45,8 @@ constexpr int M2_CAP = 8192;          // larger merge class capacity
 constexpr int M_THREADS = 256;
 constexpr int M_MAXL = 64;            // merge class: at most this many neighbour lists
 constexpr int BM_THREADS = 1024;
-constexpr int BM_MAX_WORDS = 53 * 1024;  // bitmap window: 212 KB + 6.6 KB summary
-constexpr int BM_WARP_PER_LIST = 128;    // rows with this many neighbours: warp per list
+constexpr int BM_MAX_WORDS = 52 * 1024;  // bitmap window: 208 KB + 6.5 KB summary + 12 KB counters/bounds
+constexpr int BM_WARP_PER_LIST = 128;    // bitmap rows with this many neighbours are hubs (queued first)
 
 enum { Q_WARP = 0, Q_W2 = 1, Q_COPY = 2, Q_BITMAP = 3, Q_MERGE = 4, Q_MERGE2 = 5, Q_HUB = 6,
        Q_MERGE0 = 7, NQ = 8 };
@@ -290,6 +290,9 @@ struct LightArgs {
     int32_t* cnt;
     Counters* ctr;
     uint32_t* status;
+    const int2* ybl;           // bitmap rows: per y, (start in szcol, length) of S[b]
+    const int2* ybh;           // per y, the list a heavy x reads: light z of a heavy y as
+                               // (-(offset in slcol) - 1, length), else as ybl
 };
 
 // ------------------------------------------------------------ warp classes
@@ -689,32 +692,115 @@ __global__ void __launch_bounds__(M_THREADS)
 }
 
 // ------------------------------------------------------------ bitmap class
-__device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, int32_t r) {
-    const int32_t wi = r >> 5;
-    const uint32_t old = atomicOr(&bm[wi], 1u << (r & 31));
-    if (old == 0) atomicOr(&summ[wi >> 5], 1u << (wi & 31));
+// Per y, the neighbour list a light x and a heavy x read (light z only from a
+// heavy y), so that the bitmap kernel finds a list's bounds with one load.
+__global__ void ybounds_kernel(int64_t ny, const int32_t* __restrict__ syoff,
+                               const int32_t* __restrict__ hy, const int32_t* __restrict__ sloff,
+                               int2* __restrict__ ybl, int2* __restrict__ ybh) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ny;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int2 l = make_int2(syoff[b], syoff[b + 1] - syoff[b]);
+        ybl[b] = l;
+        const int32_t j = hy[b];
+        ybh[b] = j >= 0 ? make_int2(-sloff[j] - 1, sloff[j + 1] - sloff[j]) : l;
+    }
 }
 
-// Persistent blocks, one x at a time.  The bitmap and its summary start at
-// zero and are cleared word by word as they are emitted.
+// Set bit r; a bit that was clear is a new distinct value of the row, counted
+// for the thread that owns its word in the emission (owner_shift: log2 of the
+// words a thread owns).
+__device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t* own, int owner_shift,
+                                     int32_t r) {
+    const int32_t wi = r >> 5;
+    const uint32_t bit = 1u << (r & 31);
+    const uint32_t old = atomicOr(&bm[wi], bit);
+    if (old == 0) atomicOr(&summ[wi >> 5], 1u << (wi & 31));
+    if (!(old & bit)) atomicAdd(&own[wi >> owner_shift], 1u);
+}
+
+// Exclusive prefix over a 1024-thread block; *total gets the block's sum.
+// Two barriers; sw holds 32 words.
+__device__ __forceinline__ uint32_t bm_block_scan(uint32_t v, uint32_t* sw, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sw[warp] = inc;
+    __syncthreads();
+    const uint32_t x = sw[lane];
+    uint32_t before = lane < warp ? x : 0u, tot = x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    *total = tot;
+    __syncthreads();
+    return before + inc - v;
+}
+
+// Lane whose exclusive prefix ex starts the run holding j: the last lane with
+// ex <= j (a lane whose count is 0 is never returned for j below the total).
+__device__ __forceinline__ int run_owner(uint32_t ex, uint32_t j) {
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t e = __shfl_sync(0xffffffffu, ex, owner + step);
+        if (e <= j) owner += step;
+    }
+    return owner;
+}
+
+// Persistent blocks of 1024 threads, one x at a time; the rows come from a
+// work counter, hubs first.  Shared memory (dynamic): the bitmap window, its
+// summary (one bit per non-zero bitmap word), a distinct-value counter per
+// thread, and the current chunk's list bounds.  The bitmap, the summary and
+// the counters start at zero and are cleared as they are emitted.
+//
+// Thread t owns the 32 * spt bitmap words of summary words [t * spt,
+// (t + 1) * spt); its output run is their set bits in z order.  Marking
+// counts every bit that goes from clear to set for the owning thread, so
+// each thread knows its run's length without a pass over the bitmap.
+//
+// Marking: the row's neighbour lists are taken 1024 at a time, one per
+// thread (bounds from the per-y tables, prefix-summed over the block); thread
+// t then takes flat candidates t, t + 1024, ... (adjacent threads read
+// adjacent list entries) and finds each one's list by a 10-step search over
+// the chunk's prefix sums.  A heavy row's product row (bit l of G means
+// (a, hz_inv[l]) is an output) is expanded by all warps, 32 words at a time.
+// Emission: rows with up to BM_DENSE values are written by each thread
+// walking its own words; denser rows by warps, each over the words of its 32
+// threads, 32 words at a time with coalesced stores.
+constexpr int BM_CHUNK = 1024;           // neighbour lists per marking chunk
+constexpr uint32_t BM_DENSE = 160000;    // rows with more values are emitted by warps
+
 __global__ void __launch_bounds__(BM_THREADS, 1)
     light_bitmap_kernel(LightArgs A, const int32_t* hub_queue, const int32_t* queue,
                         const Counters* qc, int32_t win_words) {
     extern __shared__ uint32_t smem_bm[];
-    uint32_t* bm = smem_bm;                       // win_words
-    uint32_t* summ = smem_bm + win_words;         // win_words / 32
+    uint32_t* bm = smem_bm;                          // win_words (a multiple of 32)
+    uint32_t* summ = smem_bm + win_words;            // win_words / 32
+    uint32_t* own = summ + win_words / 32;           // BM_THREADS
+    uint32_t* s_pre = own + BM_THREADS;              // BM_CHUNK
+    int32_t* s_start = reinterpret_cast<int32_t*>(s_pre + BM_CHUNK);   // BM_CHUNK
     __shared__ uint32_t sw[32];
     __shared__ unsigned long long s_base;
-    __shared__ uint32_t s_pre[BM_THREADS];     // prefix of the neighbour list lengths
-    __shared__ int32_t s_start[BM_THREADS];    // list start (negative: in slcol)
     __shared__ uint32_t s_item[2];             // work items of this row and the next
-    __shared__ uint32_t s_total;               // candidates of a flattened row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nh = qc->q[Q_HUB], nq = nh + qc->q[Q_BITMAP];
     const int64_t win_bits = (int64_t)win_words * 32;
-    for (int32_t i = threadIdx.x; i < win_words + win_words / 32; i += blockDim.x) smem_bm[i] = 0;
-    // rows are taken from a global counter, hubs first (longest work first);
-    // the next row's item is fetched while this one is processed, into the
-    // other slot of s_item
+    const int32_t nsumm_win = win_words / 32;
+    // words per thread: spt summary words, a power of two
+    int32_t spt = 1, owner_shift = 5;
+    while (spt * BM_THREADS < nsumm_win) {
+        spt <<= 1;
+        ++owner_shift;
+    }
+    for (int32_t i = threadIdx.x; i < win_words + nsumm_win + BM_THREADS; i += blockDim.x)
+        smem_bm[i] = 0;
     if (threadIdx.x == 0) s_item[0] = atomicAdd(&A.ctr->bm_next, 1u);
     __syncthreads();
     for (uint32_t r = 0;; ++r) {
@@ -724,16 +810,16 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
         const int32_t a = qi < nh ? hub_queue[qi] : queue[qi - nh];
         const int32_t h = A.hx[a];
         const bool heavy = h >= 0;
+        const int2* yb = heavy ? A.ybh : A.ybl;
         const int32_t e0 = A.rxoff[a], deg = A.rxoff[a + 1] - e0;
         unsigned long long ub = (unsigned long long)A.cand[a] +
                                 (heavy ? (unsigned long long)A.w : 0ull);
         if (ub > (unsigned long long)A.nz) ub = (unsigned long long)A.nz;
-        // the reservation's result is read only after the marking phase's
-        // barrier, so its latency overlaps the marking
+        // read only after the marking phase's barriers: its latency overlaps them
         if (threadIdx.x == 0) s_base = atomicAdd(&A.ctr->cursor, ub);
-        unsigned long long base = 0;
-        bool room = true;
         unsigned long long running = 0;
+        bool room = true;
+        unsigned long long base = 0;
         // the z ids a row can reach: its query's range in a batch (x and z ids
         // of one query coincide), else the whole domain
         int64_t zr0 = 0, zr1 = A.nz;
@@ -750,104 +836,18 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
             const int64_t zend = min(zr1, z0 + win_bits);
             const int32_t nwords = (int32_t)((zend - z0 + 31) >> 5);
             const int32_t nsumm = (nwords + 31) >> 5;
-            // rows with many neighbours (the hubs): each warp takes 32 neighbour
-            // lists at a time, its lanes read the 32 lists' bounds at once, and
-            // the warp walks their candidates flat (lane l takes flat
-            // candidates l, l + 32, ...; the owning list is found by a binary
-            // search over the lanes' prefix sums with shuffles)
-            if (deg >= BM_WARP_PER_LIST) {
-                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                for (int32_t t0 = warp * 32; t0 < deg; t0 += BM_THREADS) {
-                    int32_t start = 0, L = 0;   // start < 0: -(offset in slcol) - 1
-                    if (t0 + lane < deg) {
-                        const int32_t b = A.rycol[e0 + t0 + lane];
-                        const int32_t j = heavy ? A.hy[b] : -1;
-                        if (j >= 0) {
-                            start = -A.sloff[j] - 1;
-                            L = A.sloff[j + 1] - A.sloff[j];
-                        } else {
-                            start = A.syoff[b];
-                            L = A.syoff[b + 1] - start;
-                        }
-                    }
-                    int32_t incl = L;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const int32_t excl = incl - L;
-                    const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                    constexpr int UH = 8;
-                    for (int32_t f0 = 0; f0 < total; f0 += 32 * UH) {
-                        int32_t zz[UH];
-#pragma unroll
-                        for (int u = 0; u < UH; ++u) {
-                            const int32_t f = f0 + 32 * u + lane;
-                            int owner = 0;              // last lane with excl <= f
-#pragma unroll
-                            for (int step = 16; step > 0; step >>= 1) {
-                                const int32_t e = __shfl_sync(0xffffffffu, excl, owner + step);
-                                if (e <= f) owner += step;
-                            }
-                            const int32_t st = __shfl_sync(0xffffffffu, start, owner);
-                            const int32_t off = f - __shfl_sync(0xffffffffu, excl, owner);
-                            zz[u] = -1;
-                            if (f < total) zz[u] = st >= 0 ? A.szcol[st + off] : A.slcol[-st - 1 + off];
-                        }
-#pragma unroll
-                        for (int u = 0; u < UH; ++u)
-                            if (zz[u] >= z0 && zz[u] < zend) mark(bm, summ, (int32_t)(zz[u] - z0));
-                    }
-                }
-            }
-            // other rows (fewer than BM_WARP_PER_LIST = 128 neighbour lists):
-            // warp 0 reads the lists' bounds (four per lane) and prefix-sums
-            // their lengths; then thread t handles flat candidates t,
-            // t + BM_THREADS, ... (adjacent threads read adjacent list entries)
-            if (deg < BM_WARP_PER_LIST) {
-                if (threadIdx.x < 32) {
-                    const int lane = threadIdx.x;
-                    int32_t st4[4], L4[4], sum = 0;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int i = 4 * lane + k;
-                        st4[k] = 0;
-                        L4[k] = 0;
-                        if (i < deg) {
-                            const int32_t b = A.rycol[e0 + i];
-                            const int32_t j = heavy ? A.hy[b] : -1;
-                            if (j >= 0) {      // light z of a heavy y: negative = slcol offset
-                                st4[k] = -A.sloff[j] - 1;
-                                L4[k] = A.sloff[j + 1] - A.sloff[j];
-                            } else {
-                                st4[k] = A.syoff[b];
-                                L4[k] = A.syoff[b + 1] - st4[k];
-                            }
-                        }
-                        sum += L4[k];
-                    }
-                    int32_t inc = sum;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                        if (lane >= o) inc += y;
-                    }
-                    int32_t run = inc - sum;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int i = 4 * lane + k;
-                        if (i < deg) {
-                            s_pre[i] = (uint32_t)run;
-                            s_start[i] = st4[k];
-                        }
-                        run += L4[k];
-                    }
-                    if (lane == 31) s_total = (uint32_t)inc;
-                }
+            // ---- mark the light candidates, 1024 neighbour lists at a time
+            for (int32_t c0 = 0; c0 < deg; c0 += BM_CHUNK) {
+                const int32_t n = min(BM_CHUNK, deg - c0);
+                int2 bl = make_int2(0, 0);   // (start, length); start < 0: -(offset in slcol) - 1
+                if ((int32_t)threadIdx.x < n) bl = yb[A.rycol[e0 + c0 + threadIdx.x]];
+                uint32_t total;
+                const uint32_t ex = bm_block_scan((uint32_t)bl.y, sw, &total);
+                // entries past the chunk's lists hold the total, so the search
+                // over all BM_CHUNK entries never selects them
+                s_pre[threadIdx.x] = (int32_t)threadIdx.x < n ? ex : total;
+                s_start[threadIdx.x] = bl.x;
                 __syncthreads();
-                const uint32_t total = s_total;
-                const int32_t nn = deg;
                 constexpr int U = 8;    // candidates loaded before any is marked
                 for (uint32_t f0 = threadIdx.x; f0 < total; f0 += U * BM_THREADS) {
                     int32_t zz[U];
@@ -856,100 +856,122 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                         const uint32_t f = f0 + (uint32_t)u * BM_THREADS;
                         zz[u] = -1;
                         if (f < total) {
-                            int32_t lo = 0, hi = nn;   // last k with s_pre[k] <= f
-                            while (hi - lo > 1) {
-                                const int32_t mid = (lo + hi) >> 1;
-                                if (s_pre[mid] <= f) lo = mid; else hi = mid;
-                            }
-                            const int32_t st0 = s_start[lo];
-                            const uint32_t off = f - s_pre[lo];
+                            int32_t k = 0;      // last k with s_pre[k] <= f (s_pre[0] = 0)
+#pragma unroll
+                            for (int step = BM_CHUNK / 2; step > 0; step >>= 1)
+                                if (s_pre[k + step] <= f) k += step;
+                            const int32_t st0 = s_start[k];
+                            const uint32_t off = f - s_pre[k];
                             zz[u] = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u)
-                        if (zz[u] >= z0 && zz[u] < zend) mark(bm, summ, (int32_t)(zz[u] - z0));
+                        if (zz[u] >= z0 && zz[u] < zend)
+                            mark(bm, summ, own, owner_shift, (int32_t)(zz[u] - z0));
                 }
-                // s_pre and s_start are next written after the barrier that ends
-                // the marking phase below
+                __syncthreads();        // s_pre / s_start are rewritten by the next chunk
             }
-            // heavy product row: bit l of G[h] means (a, hz_inv[l]) is an output
+            // ---- heavy product row, 32 words per warp step
             if (heavy && A.G) {
                 const int32_t gw = (int32_t)((A.w + 31) >> 5);
                 const uint32_t* grow = A.G + (int64_t)h * A.g_stride;
-                for (int32_t i = threadIdx.x; i < gw; i += blockDim.x) {
-                    uint32_t bits = grow[i];
-                    while (bits) {
-                        const int bt = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const int64_t l = (int64_t)i * 32 + bt;
-                        if (l < A.w) {
-                            const int64_t z = A.hz_inv[l];
-                            if (z >= z0 && z < zend) mark(bm, summ, (int32_t)(z - z0));
+                for (int32_t i0 = warp * 32; i0 < gw; i0 += BM_THREADS) {
+                    const int32_t i = i0 + lane;
+                    const uint32_t wd = i < gw ? grow[i] : 0u;
+                    const uint32_t c = __popc(wd);
+                    uint32_t inc = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    const uint32_t T = __shfl_sync(0xffffffffu, inc, 31), exl = inc - c;
+                    for (uint32_t j0 = 0; j0 < T; j0 += 32) {
+                        const uint32_t j = j0 + lane;
+                        const int owner = run_owner(exl, j);
+                        const uint32_t ow = __shfl_sync(0xffffffffu, wd, owner);
+                        const uint32_t oe = __shfl_sync(0xffffffffu, exl, owner);
+                        if (j < T) {
+                            const int bt = (int)__fns(ow, 0u, (int)(j - oe) + 1);
+                            const int64_t l = (int64_t)(i0 + owner) * 32 + bt;
+                            if (l < A.w) {
+                                const int64_t z = A.hz_inv[l];
+                                if (z >= z0 && z < zend)
+                                    mark(bm, summ, own, owner_shift, (int32_t)(z - z0));
+                            }
                         }
                     }
                 }
             }
             __syncthreads();
+            // ---- emit the set bits in z order
+            const uint32_t mine = own[threadIdx.x];
+            own[threadIdx.x] = 0;
+            uint32_t D;
+            const uint32_t myex = bm_block_scan(mine, sw, &D);
             base = s_base;
             room = base + ub <= (unsigned long long)A.tmp_cap;
-            if (!room && z0 == 0 && threadIdx.x == 0) atomicOr(A.status, ST_OVERFLOW);
-            // emit set bits in z order: blocked ranges of summary words
-            const int32_t spt = (nsumm + blockDim.x - 1) / blockDim.x;
-            const int32_t lo = min(nsumm, (int32_t)threadIdx.x * spt);
-            const int32_t hi = min(nsumm, lo + spt);
-            uint32_t mine = 0;
-            for (int32_t s = lo; s < hi; ++s) {
-                uint32_t sm = summ[s];
-                while (sm) {
-                    const int j = __ffs(sm) - 1;
-                    sm &= sm - 1;
-                    mine += __popc(bm[s * 32 + j]);
-                }
-            }
-            // exclusive prefix of the threads' counts: warp scans, then the warp
-            // totals through shared memory (one barrier)
-            uint32_t ex, tot;
-            {
-                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                uint32_t inc = mine;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                if (lane == 31) sw[warp] = inc;
-                __syncthreads();
-                const uint32_t v = lane < BM_THREADS / 32 ? sw[lane] : 0u;
-                uint32_t before = lane < warp ? v : 0u;
-                tot = v;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    before += __shfl_xor_sync(0xffffffffu, before, o);
-                    tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                }
-                ex = before + inc - mine;
-            }
-            unsigned long long p = base + running + ex;
+            if (!room && z0 == zr0 && threadIdx.x == 0) atomicOr(A.status, ST_OVERFLOW);
             const unsigned long long lim = base + ub;
-            for (int32_t s = lo; s < hi; ++s) {
-                uint32_t sm = summ[s];
-                summ[s] = 0;
-                while (sm) {
-                    const int j = __ffs(sm) - 1;
-                    sm &= sm - 1;
-                    const int32_t wi = s * 32 + j;
-                    uint32_t bits = bm[wi];
-                    bm[wi] = 0;
-                    while (bits) {
-                        const int bt = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        if (room && p < lim) A.tmp[p] = (int32_t)(z0 + (int64_t)wi * 32 + bt);
-                        ++p;
+            const int32_t slo = min(nsumm, (int32_t)threadIdx.x * spt);
+            const int32_t shi = min(nsumm, slo + spt);
+            if (D <= BM_DENSE) {
+                unsigned long long p = base + running + myex;
+                for (int32_t s = slo; s < shi; ++s) {
+                    uint32_t m = summ[s];
+                    summ[s] = 0;
+                    while (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int32_t wi = s * 32 + j;
+                        uint32_t bits = bm[wi];
+                        bm[wi] = 0;
+                        while (bits) {
+                            const int bt = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            if (room && p < lim) A.tmp[p] = (int32_t)(z0 + (int64_t)wi * 32 + bt);
+                            ++p;
+                        }
                     }
                 }
+            } else {
+                // the warp's words are those of its 32 threads; its run starts
+                // where its first thread's does
+                unsigned long long p = base + running + __shfl_sync(0xffffffffu, myex, 0);
+                const int32_t g0 = min(nsumm, warp * 32 * spt);
+                const int32_t g1 = min(nsumm, g0 + 32 * spt);
+                for (int32_t g = g0; g < g1; ++g) {
+                    if (summ[g] == 0) continue;
+                    const int32_t wi = g * 32 + lane;
+                    const uint32_t wd = bm[wi];
+                    bm[wi] = 0;
+                    const uint32_t c = __popc(wd);
+                    uint32_t inc = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += y;
+                    }
+                    const uint32_t T = __shfl_sync(0xffffffffu, inc, 31), exl = inc - c;
+                    for (uint32_t j0 = 0; j0 < T; j0 += 32) {
+                        const uint32_t j = j0 + lane;
+                        const int owner = run_owner(exl, j);
+                        const uint32_t ow = __shfl_sync(0xffffffffu, wd, owner);
+                        const uint32_t oe = __shfl_sync(0xffffffffu, exl, owner);
+                        if (j < T) {
+                            const int bt = (int)__fns(ow, 0u, (int)(j - oe) + 1);
+                            const unsigned long long o = p + j;
+                            if (room && o < lim)
+                                A.tmp[o] = (int32_t)(z0 + (int64_t)(g * 32 + owner) * 32 + bt);
+                        }
+                    }
+                    p += T;
+                    __syncwarp();
+                    if (lane == 0) summ[g] = 0;
+                }
             }
-            running += tot;
+            running += D;
             __syncthreads();
         }
         if (threadIdx.x == 0) {
@@ -1036,6 +1058,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     A.cnt = lr.cnt;
     A.ctr = ctr;
     A.status = d_status;
+    A.ybl = nullptr;
+    A.ybh = nullptr;
 
     if (hc.q[Q_WARP]) {
         const size_t sm = (size_t)8 * W_CAP * sizeof(int32_t);
@@ -1082,12 +1106,21 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         tend(TM_LIGHT_MERGE);
     }
     if (hc.q[Q_BITMAP] + hc.q[Q_HUB]) {
+        int2* ybl = ws.get<int2>((size_t)g.ny + 1);
+        int2* ybh = ws.get<int2>((size_t)g.ny + 1);
+        if (g.ny > 0) {
+            ybounds_kernel<<<grid_for(g.ny, 256, 152 * 8), 256, 0, st>>>(g.ny, g.syoff, p.hy, p.sloff,
+                                                                          ybl, ybh);
+            JP_CHECK_LAUNCH();
+        }
+        A.ybl = ybl;
+        A.ybh = ybh;
         int64_t words = (g.nz + 31) / 32;
         int32_t win = (int32_t)std::min<int64_t>(words, BM_MAX_WORDS);
-        win = (win + 1023) & ~1023;                 // whole summary words
-        const size_t sm = (size_t)(win + win / 32) * sizeof(uint32_t);
+        win = (win + 31) & ~31;                     // whole summary words
+        const size_t sm = (size_t)(win + win / 32 + BM_THREADS + 2 * BM_CHUNK) * sizeof(uint32_t);
         smem_limit((const void*)light_bitmap_kernel,
-                   (BM_MAX_WORDS + BM_MAX_WORDS / 32) * sizeof(uint32_t));
+                   (BM_MAX_WORDS + BM_MAX_WORDS / 32 + BM_THREADS + 2 * BM_CHUNK) * sizeof(uint32_t));
         tbegin(TM_LIGHT_BITMAP);
         light_bitmap_kernel<<<grid_for(hc.q[Q_BITMAP] + hc.q[Q_HUB], 1, 152), BM_THREADS, sm, st>>>(
             A, queues + (int64_t)Q_HUB * nx, queues + (int64_t)Q_BITMAP * nx, ctr, win);
