@@ -120,8 +120,112 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- oracle baseline
+# The oracle is timed on the host cores on rows of the same relation.  What it
+# needs once per relation -- S sorted by y, R grouped by x -- is built before
+# the clock starts, so the timed work is the per-row join, sort and unique.
+# Rows are a stratified sample: every k-th x in decreasing candidate order
+# (the largest x included), so hubs and light rows keep their shares.
+def rows_csr(rx, ry):
+    """Distinct tuples of R grouped by x: (x values, row offsets, y values)."""
+    key = np.unique((rx.astype(np.int64) << 32) | (ry.astype(np.int64) & 0xFFFFFFFF))
+    x = (key >> 32).astype(np.int32)
+    y = (key & 0xFFFFFFFF).astype(np.uint32).astype(np.int32)
+    ux, start = np.unique(x, return_index=True)
+    return ux, np.append(start, len(x)).astype(np.int64), y
+
+
+def stratified_rows(cand, target):
+    """Row indices (sorted): every k-th row in decreasing candidate order, k set by target."""
+    order = np.argsort(-cand, kind="stable")
+    k = max(1, int(round(float(cand.sum()) / max(target, 1.0))))
+    return np.sort(order[::k]), k
+
+
+def split_rows(rows, cand, parts):
+    """Consecutive groups of rows with about equal candidate counts."""
+    if len(rows) == 0:
+        return []
+    cum = np.cumsum(cand[rows])
+    cuts = np.searchsorted(cum, cum[-1] * np.arange(1, parts) / parts, side="right")
+    return [g for g in np.split(rows, cuts) if len(g)]
+
+
+def sub_csr(off, y, rows):
+    lens = off[rows + 1] - off[rows]
+    sub_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    idx = np.repeat(off[rows] - sub_off[:-1], lens) + np.arange(int(sub_off[-1]))
+    return sub_off, y[idx]
+
+
+_POOL_S = None
+
+
+def _pool_init(sy, sz):
+    global _POOL_S
+    import oracle
+
+    class _S:
+        pass
+    _POOL_S = _S()
+    _POOL_S.y, _POOL_S.z = sy, sz
+    oracle.build()
+
+
+def _pool_rows(args):
+    import oracle
+    sub_off, sub_y, cap = args
+    z, _ = oracle.two_path_rows(sub_off, sub_y, _POOL_S, cap_hint=cap)
+    return len(z)
+
+
+class OracleRows:
+    """The oracle's per-row join over R's rows, single-threaded or on a process pool."""
+
+    def __init__(self, rx, ry, procs=1):
+        import oracle
+        oracle.build()
+        self.ux, self.off, self.y = rows_csr(rx, ry)
+        self.S = oracle.SortedS(rx, ry)
+        ys, cy = np.unique(self.S.y, return_counts=True)
+        deg = np.zeros(len(self.y), np.float64)
+        at = np.searchsorted(ys, self.y)
+        ok = (at < len(ys)) & (ys[np.minimum(at, len(ys) - 1)] == self.y)
+        deg[ok] = cy[at[ok]]
+        self.cand = np.add.reduceat(deg, self.off[:-1]) if len(self.y) else np.zeros(0)
+        self.procs = procs
+        self.pool = None
+        if procs > 1:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(procs, _pool_init, (self.S.y, self.S.z))
+            self.pool.map(_pool_rows, [(np.zeros(1, np.int64), np.zeros(0, np.int32), 1)] * procs)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def run(self, rows):
+        """Distinct pairs of the given rows and the wall seconds the oracle took."""
+        import oracle
+        if self.pool is None:
+            sub_off, sub_y = sub_csr(self.off, self.y, rows)
+            t = time.perf_counter()
+            z, _ = oracle.two_path_rows(sub_off, sub_y, self.S, cap_hint=int(self.cand[rows].sum()))
+            return len(z), time.perf_counter() - t
+        groups = split_rows(rows, self.cand, 8 * self.procs)
+        tasks = []
+        for g in groups:
+            so, sy = sub_csr(self.off, self.y, g)
+            tasks.append((so, sy, int(self.cand[g].sum())))
+        t = time.perf_counter()
+        n = sum(self.pool.map(_pool_rows, tasks, chunksize=1))
+        return n, time.perf_counter() - t
+
+
 def cpu_sample(rx, ry, target_cand):
-    """Prefix of x values whose join candidates add up to about target_cand."""
+    """Prefix of x values whose join candidates add up to about target_cand (the set
+    similarity join's oracle sample, which needs the witness counts of whole x ranges)."""
     ux, cand = candidate_counts(rx, ry)
     cum = np.cumsum(cand)
     k = int(np.searchsorted(cum, target_cand)) + 1
@@ -129,21 +233,50 @@ def cpu_sample(rx, ry, target_cand):
     return int(ux[0]), int(ux[k - 1]), k, float(cum[k - 1]), len(ux), float(cum[-1])
 
 
-def run_oracle_sample(rx, ry, lo, hi):
-    import oracle
-    oracle.build()
-    t = time.perf_counter()
-    ox, oz = oracle.two_path(rx, ry, x_lo=lo, x_hi=hi)
-    return len(ox), time.perf_counter() - t
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
-def cpu_baseline(rx, ry, target_cand=3.0e7):
-    lo, hi, k, c, nx, ctot = cpu_sample(rx, ry, target_cand)
-    n, secs = run_oracle_sample(rx, ry, lo, hi)
-    return {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"x values {lo}..{hi} ({k} of {nx} x values, {c:.3g} of {ctot:.3g} join "
-                       f"candidates), single-threaded C oracle incl. its sort of R and S; "
-                       f"{n} distinct pairs in {secs:.2f}s")}
+def cpu_baseline(rx, ry, target_cand=3.0e8, full=False):
+    """The oracle on the host cores: one core on a stratified sample, all cores on a sample
+    as many times larger (or, with full, on every row)."""
+    procs = os.cpu_count() or 1
+    one = OracleRows(rx, ry, 1)
+    rows1, k1 = stratified_rows(one.cand, target_cand)
+    n1, s1 = one.run(rows1)
+    c1 = float(one.cand[rows1].sum())
+    res = {"value": n1 / s1, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"every {k1}-th x in decreasing candidate order ({len(rows1)} of "
+                      f"{len(one.ux)} x values, {c1:.3g} of {one.cand.sum():.3g} join candidates, "
+                      f"the largest x included); S sorted and R grouped once before timing; "
+                      f"{n1} distinct pairs in {s1:.2f}s"),
+           "cpu": cpu_model()}
+    if procs > 1:
+        many = OracleRows(rx, ry, procs)
+        try:
+            if full:
+                rowsP, kP = np.arange(len(many.ux)), 1
+            else:
+                rowsP, kP = stratified_rows(many.cand, target_cand * procs)
+            nP, sP = many.run(rowsP)
+        finally:
+            many.close()
+        cP = float(many.cand[rowsP].sum())
+        res["all_cores"] = {
+            "value": nP / sP, "unit": UNIT, "cores": procs,
+            "sample": ("every x of the relation" if full else
+                       f"every {kP}-th x in decreasing candidate order ({len(rowsP)} x values, "
+                       f"{cP:.3g} join candidates)") +
+                      f"; {procs} processes over groups of rows; {nP} distinct pairs in {sP:.2f}s"}
+    return res
 
 
 # ----------------------------------------------------------------- roofline
@@ -379,7 +512,7 @@ def run_ours(args, rank, world, local_rank):
 
     base = None
     if rank == 0 and not args.no_cpu:
-        base = cpu_baseline(rx, ry)
+        base = cpu_baseline(rx, ry, args.cpu_cand, full=args.cpu_full)
 
     peaks, kind = load_peaks()
     peaks.update(tensor_peaks)
@@ -639,24 +772,32 @@ def run_ssj(args):
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The oracle on all host cores, each step a stratified sample of the workload's rows."""
     rx, ry, wl = make_workload(args.workload)
-    lo, hi, k, c, nx, ctot = cpu_sample(rx, ry, args.ref_cand)
-    for _ in range(args.warmup):
-        run_oracle_sample(rx, ry, lo, hi)
-    times, n = [], 0
-    for _ in range(args.steps):
-        n, secs = run_oracle_sample(rx, ry, lo, hi)
-        times.append(secs)
+    procs = os.cpu_count() or 1
+    orc = OracleRows(rx, ry, procs)
+    try:
+        rows, k = stratified_rows(orc.cand, args.ref_cand)
+        for _ in range(args.warmup):
+            orc.run(rows)
+        times, n = [], 0
+        for _ in range(args.steps):
+            n, secs = orc.run(rows)
+            times.append(secs)
+    finally:
+        orc.close()
     secs = sum(times) / len(times)
     value = n / secs
-    sample = (f"x values {lo}..{hi} ({k} of {nx} x values, {c:.3g} of {ctot:.3g} join candidates) "
-              f"per step, single-threaded C oracle; {n} distinct pairs")
+    c = float(orc.cand[rows].sum())
+    sample = (f"every {k}-th x in decreasing candidate order ({len(rows)} of {len(orc.ux)} x values, "
+              f"{c:.3g} of {orc.cand.sum():.3g} join candidates) per step; C oracle on {procs} "
+              f"processes, S sorted and R grouped once before timing; {n} distinct pairs")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": {"workload": args.workload, "n_tuples": wl["n"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -676,7 +817,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip timing the query at the shipped predictor's thresholds")
-    ap.add_argument("--ref-cand", type=float, default=1.5e7)
+    ap.add_argument("--ref-cand", type=float, default=4.0e8,
+                    help="join candidates per step of the reference arm (all host cores)")
+    ap.add_argument("--cpu-cand", type=float, default=3.0e8,
+                    help="join candidates of the single-core oracle sample (x cores for all cores)")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time the all-cores oracle over every row of the relation")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

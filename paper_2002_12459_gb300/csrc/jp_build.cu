@@ -123,6 +123,55 @@ __global__ void out_join_kernel(const int32_t* a, const int32_t* b, int64_t n,
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(acc, s);
 }
 
+// xsum[a] = sum over the y of R[a] of deg_S(y): lane per x; the x of a warp
+// with more than 32 neighbours are summed by the whole warp, one after another
+__global__ void xsum_kernel(int64_t nx, const int32_t* __restrict__ rxoff,
+                            const int32_t* __restrict__ rycol, const int32_t* __restrict__ deg_sy,
+                            int64_t* __restrict__ xsum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < nx;
+         base += stride) {
+        const int64_t a = base + lane;
+        const bool valid = a < nx;
+        int32_t e0 = 0, e1 = 0;
+        if (valid) {
+            e0 = rxoff[a];
+            e1 = rxoff[a + 1];
+        }
+        const bool small = valid && e1 - e0 <= 32;
+        long long c = 0;
+        if (small) {
+            int32_t e = e0;
+            for (; e + 4 <= e1; e += 4) {
+                const int32_t b0 = rycol[e], b1 = rycol[e + 1], b2 = rycol[e + 2], b3 = rycol[e + 3];
+                c += (long long)deg_sy[b0] + deg_sy[b1] + deg_sy[b2] + deg_sy[b3];
+            }
+            for (; e < e1; ++e) c += deg_sy[rycol[e]];
+        }
+        unsigned big = __ballot_sync(0xffffffffu, valid && !small);
+        while (big) {
+            const int j = __ffs(big) - 1;
+            big &= big - 1;
+            const int32_t f0 = __shfl_sync(0xffffffffu, e0, j), f1 = __shfl_sync(0xffffffffu, e1, j);
+            long long sj = 0;
+            int32_t e = f0 + lane;
+            for (; e + 7 * 32 < f1; e += 8 * 32) {
+                int32_t b[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) b[u] = rycol[e + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sj += deg_sy[b[u]];
+            }
+            for (; e < f1; e += 32) sj += deg_sy[rycol[e]];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
+            if (lane == j) c = sj;
+        }
+        if (valid) xsum[a] = (int64_t)c;
+    }
+}
+
 inline int G(int64_t n) { return grid_for(n, 256, 152 * 16); }
 
 // Sort + unique 64-bit keys; returns the unique keys buffer and count.
@@ -297,6 +346,14 @@ void build_graph(const jp_rel* R, const jp_rel* S, Graph& g, Arena& ws, cudaStre
         if (g.ny > 0) { deg_from_off_kernel<<<G(g.ny), 256, 0, st>>>(g.syoff, g.ny, g.deg_sy); JP_CHECK_LAUNCH(); }
         if (g.nr > 0) { deg_hist_kernel<<<G(g.nr), 256, 0, st>>>(g.rycol, g.nr, g.deg_ry); JP_CHECK_LAUNCH(); }
         if (g.ns > 0) { deg_hist_kernel<<<G(g.ns), 256, 0, st>>>(g.szcol, g.ns, g.deg_sz); JP_CHECK_LAUNCH(); }
+    }
+    // every x's join candidates, read by threshold selection and by the light
+    // part's classification
+    g.xsum = ws.get<int64_t>(g.nx + 1);
+    if (g.nx > 0) {
+        xsum_kernel<<<grid_for(g.nx, 256, 152 * 16), 256, 0, st>>>(g.nx, g.rxoff, g.rycol, g.deg_sy,
+                                                                  g.xsum);
+        JP_CHECK_LAUNCH();
     }
     // |OUT_join| = sum_y deg_R(y) deg_S(y)
     unsigned long long* acc = ws.get<unsigned long long>(1);

@@ -107,6 +107,7 @@ struct Graph {
     int32_t* deg_ry = nullptr;     // [ny]
     int32_t* deg_sy = nullptr;     // [ny]
     int32_t* deg_sz = nullptr;     // [nz]
+    int64_t* xsum = nullptr;       // [nx] sum over x's y of deg_S(y): x's join candidates (may be null)
     double out_join = 0;
 };
 

@@ -66,21 +66,29 @@ __device__ __forceinline__ uint32_t next_pow2(uint32_t v) {
     return v <= 1 ? 1u : 1u << (32 - __clz(v - 1));
 }
 
-__device__ __forceinline__ int64_t cand_of(int32_t b, bool heavy, const int32_t* hy,
-                                           const int32_t* sloff, const int32_t* deg_sy) {
-    if (heavy) {
-        int32_t j = hy[b];
-        if (j >= 0) return sloff[j + 1] - sloff[j];
+// Per y, the neighbour list a light x and a heavy x read (light z only from a
+// heavy y), so that the bitmap kernel finds a list's bounds with one load.
+__global__ void ybounds_kernel(int64_t ny, const int32_t* __restrict__ syoff,
+                               const int32_t* __restrict__ hy, const int32_t* __restrict__ sloff,
+                               int2* __restrict__ ybl, int2* __restrict__ ybh) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ny;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int2 l = make_int2(syoff[b], syoff[b + 1] - syoff[b]);
+        ybl[b] = l;
+        const int32_t j = hy[b];
+        ybh[b] = j >= 0 ? make_int2(-sloff[j] - 1, sloff[j + 1] - sloff[j]) : l;
     }
-    return deg_sy[b];
 }
 
-// Candidate count c(x): lane per x, each lane summing its own lists; the x
-// of a warp with more than 32 lists are then summed by the whole warp, one
-// after another.
-__global__ void cand_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
-                            const int32_t* hx, const int32_t* hy, const int32_t* sloff,
-                            const int32_t* deg_sy, int64_t* cand) {
+// Candidate count c(x): a light x reads all of S[b] for its y, which the
+// index build already summed (xsum; recomputed here when absent); a heavy x
+// reads the lengths of the per-y lists it walks (ybh: light z only from a
+// heavy y).  Lane per x; the x of a warp with more than 32 lists are summed by
+// the whole warp, one after another.
+__global__ void cand_kernel(int64_t nx, const int32_t* __restrict__ rxoff,
+                            const int32_t* __restrict__ rycol, const int32_t* __restrict__ hx,
+                            const int2* __restrict__ ybh, const int32_t* __restrict__ deg_sy,
+                            const int64_t* __restrict__ xsum, int64_t* __restrict__ cand) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < nx;
@@ -94,18 +102,19 @@ __global__ void cand_kernel(int64_t nx, const int32_t* rxoff, const int32_t* ryc
             e1 = rxoff[a + 1];
             heavy = hx[a] >= 0;
         }
-        const bool small = valid && e1 - e0 <= 32;
-        long long c = 0;
+        const bool done = valid && !heavy && xsum;
+        const bool small = valid && !done && e1 - e0 <= 32;
+        long long c = done ? (long long)xsum[a] : 0;
         if (small) {
             int32_t e = e0;
             for (; e + 4 <= e1; e += 4) {        // four independent gathers in flight
                 const int32_t b0 = rycol[e], b1 = rycol[e + 1], b2 = rycol[e + 2], b3 = rycol[e + 3];
-                c += cand_of(b0, heavy, hy, sloff, deg_sy) + cand_of(b1, heavy, hy, sloff, deg_sy) +
-                     cand_of(b2, heavy, hy, sloff, deg_sy) + cand_of(b3, heavy, hy, sloff, deg_sy);
+                c += heavy ? (long long)ybh[b0].y + ybh[b1].y + ybh[b2].y + ybh[b3].y
+                           : (long long)deg_sy[b0] + deg_sy[b1] + deg_sy[b2] + deg_sy[b3];
             }
-            for (; e < e1; ++e) c += cand_of(rycol[e], heavy, hy, sloff, deg_sy);
+            for (; e < e1; ++e) c += heavy ? ybh[rycol[e]].y : deg_sy[rycol[e]];
         }
-        unsigned big = __ballot_sync(0xffffffffu, valid && !small);
+        unsigned big = __ballot_sync(0xffffffffu, valid && !done && !small);
         while (big) {
             const int j = __ffs(big) - 1;
             big &= big - 1;
@@ -118,9 +127,9 @@ __global__ void cand_kernel(int64_t nx, const int32_t* rxoff, const int32_t* ryc
 #pragma unroll
                 for (int u = 0; u < 8; ++u) b[u] = rycol[e + 32 * u];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) sj += cand_of(b[u], hj, hy, sloff, deg_sy);
+                for (int u = 0; u < 8; ++u) sj += hj ? ybh[b[u]].y : deg_sy[b[u]];
             }
-            for (; e < f1; e += 32) sj += cand_of(rycol[e], hj, hy, sloff, deg_sy);
+            for (; e < f1; e += 32) sj += hj ? ybh[rycol[e]].y : deg_sy[rycol[e]];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
             if (lane == j) c = sj;
@@ -692,20 +701,6 @@ __global__ void __launch_bounds__(M_THREADS)
 }
 
 // ------------------------------------------------------------ bitmap class
-// Per y, the neighbour list a light x and a heavy x read (light z only from a
-// heavy y), so that the bitmap kernel finds a list's bounds with one load.
-__global__ void ybounds_kernel(int64_t ny, const int32_t* __restrict__ syoff,
-                               const int32_t* __restrict__ hy, const int32_t* __restrict__ sloff,
-                               int2* __restrict__ ybl, int2* __restrict__ ybh) {
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ny;
-         b += (int64_t)gridDim.x * blockDim.x) {
-        const int2 l = make_int2(syoff[b], syoff[b + 1] - syoff[b]);
-        ybl[b] = l;
-        const int32_t j = hy[b];
-        ybh[b] = j >= 0 ? make_int2(-sloff[j] - 1, sloff[j + 1] - sloff[j]) : l;
-    }
-}
-
 // Set bit r; a bit that was clear is a new distinct value of the row, counted
 // for the thread that owns its word in the emission (owner_shift: log2 of the
 // words a thread owns).
@@ -1006,8 +1001,17 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     Counters* ctr = ws.get<Counters>(1);
     JP_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     tbegin(TM_CLASSIFY);
+    // per y, the list a light x and a heavy x read (bounds for the bitmap
+    // class, lengths for the candidate counts of heavy x)
+    int2* ybl = ws.get<int2>((size_t)g.ny + 1);
+    int2* ybh = ws.get<int2>((size_t)g.ny + 1);
+    if (g.ny > 0) {
+        ybounds_kernel<<<grid_for(g.ny, 256, 152 * 8), 256, 0, st>>>(g.ny, g.syoff, p.hy, p.sloff,
+                                                                      ybl, ybh);
+        JP_CHECK_LAUNCH();
+    }
     cand_kernel<<<grid_for(nx, 256, 152 * 16), 256, 0, st>>>(
-        nx, g.rxoff, g.rycol, p.hx, p.hy, p.sloff, g.deg_sy, cand);
+        nx, g.rxoff, g.rycol, p.hx, ybh, g.deg_sy, g.xsum, cand);
     JP_CHECK_LAUNCH();
     queue_kernel<<<grid_for(nx, 256, 152 * 8), 256, 0, st>>>(
         nx, cand, p.hx, g.rxoff, g.rycol, g.syoff, p.w, g.nz, queues, lr.cnt, lr.tmp_off, ctr);
@@ -1106,13 +1110,6 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         tend(TM_LIGHT_MERGE);
     }
     if (hc.q[Q_BITMAP] + hc.q[Q_HUB]) {
-        int2* ybl = ws.get<int2>((size_t)g.ny + 1);
-        int2* ybh = ws.get<int2>((size_t)g.ny + 1);
-        if (g.ny > 0) {
-            ybounds_kernel<<<grid_for(g.ny, 256, 152 * 8), 256, 0, st>>>(g.ny, g.syoff, p.hy, p.sloff,
-                                                                          ybl, ybh);
-            JP_CHECK_LAUNCH();
-        }
         A.ybl = ybl;
         A.ybh = ybh;
         int64_t words = (g.nz + 31) / 32;

@@ -34,87 +34,91 @@ struct DevHist {
 
 struct Over { long long deg; unsigned long long a, b; };
 
-// lane per x summing its own neighbours' S degrees; the x of a warp with more
-// than 32 neighbours are summed by the whole warp (eight loads in flight per
-// lane), one after another
-__global__ void hist_x_kernel(int64_t nx, const int32_t* rxoff, const int32_t* rycol,
-                              const int32_t* deg_sy, DevHist* H, Over* xo) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < nx;
-         base += stride) {
-        const int64_t a = base + lane;
-        const bool valid = a < nx;
-        int32_t e0 = 0, e1 = 0;
-        if (valid) {
-            e0 = rxoff[a];
-            e1 = rxoff[a + 1];
-        }
-        const bool small = valid && e1 - e0 <= 32;
-        unsigned long long c = 0;
-        if (small)
-            for (int32_t e = e0; e < e1; ++e) c += (unsigned long long)deg_sy[rycol[e]];
-        unsigned big = __ballot_sync(0xffffffffu, valid && !small);
-        while (big) {
-            const int j = __ffs(big) - 1;
-            big &= big - 1;
-            const int32_t f0 = __shfl_sync(0xffffffffu, e0, j), f1 = __shfl_sync(0xffffffffu, e1, j);
-            unsigned long long sj = 0;
-            int32_t e = f0 + lane;
-            for (; e + 7 * 32 < f1; e += 8 * 32) {
-                int32_t b[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) b[u] = rycol[e + 32 * u];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) sj += (unsigned long long)deg_sy[b[u]];
-            }
-            for (; e < f1; e += 32) sj += (unsigned long long)deg_sy[rycol[e]];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o);
-            if (lane == j) c = sj;
-        }
-        if (valid) {
-            const int32_t d = e1 - e0;
-            if (d <= HMAX) {
-                atomicAdd(&H->x_cnt[d], 1ull);
-                atomicAdd(&H->x_cand[d], c);
-            } else {
-                unsigned int i = atomicAdd(&H->n_xo, 1u);
-                xo[i] = Over{d, c, 0};
-            }
+// Degrees below SB are counted per block in shared memory and added to the
+// global bins once per block (most values have small degrees, so global
+// atomics on a few bins would serialise).
+constexpr int SB = 1024;
+
+// x bins: count and candidates (xsum: each x's join candidates, from the build)
+__global__ void hist_x_kernel(int64_t nx, const int32_t* __restrict__ rxoff,
+                              const int64_t* __restrict__ xsum, DevHist* H, Over* xo) {
+    __shared__ unsigned long long s_cnt[SB], s_cand[SB];
+    for (int i = threadIdx.x; i < SB; i += blockDim.x) s_cnt[i] = s_cand[i] = 0;
+    __syncthreads();
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nx;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = rxoff[a + 1] - rxoff[a];
+        const unsigned long long c = (unsigned long long)xsum[a];
+        if (d < SB) {
+            atomicAdd(&s_cnt[d], 1ull);
+            atomicAdd(&s_cand[d], c);
+        } else if (d <= HMAX) {
+            atomicAdd(&H->x_cnt[d], 1ull);
+            atomicAdd(&H->x_cand[d], c);
+        } else {
+            const unsigned int i = atomicAdd(&H->n_xo, 1u);
+            xo[i] = Over{d, c, 0};
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SB; i += blockDim.x)
+        if (s_cnt[i]) {
+            atomicAdd(&H->x_cnt[i], s_cnt[i]);
+            atomicAdd(&H->x_cand[i], s_cand[i]);
+        }
 }
 
 __global__ void hist_y_kernel(int64_t ny, const int32_t* deg_ry, const int32_t* deg_sy,
                               DevHist* H, Over* yo) {
+    __shared__ unsigned long long s_cnt[SB], s_w[SB], s_r[SB];
+    for (int i = threadIdx.x; i < SB; i += blockDim.x) s_cnt[i] = s_w[i] = s_r[i] = 0;
+    __syncthreads();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < ny;
          b += (int64_t)gridDim.x * blockDim.x) {
         const long long r = deg_ry[b], s = deg_sy[b];
         const long long d = r > s ? r : s;
         const unsigned long long wgt = (unsigned long long)(r * s);
-        if (d <= HMAX) {
+        if (d < SB) {
+            atomicAdd(&s_cnt[d], 1ull);
+            atomicAdd(&s_w[d], wgt);
+            atomicAdd(&s_r[d], (unsigned long long)r);
+        } else if (d <= HMAX) {
             atomicAdd(&H->y_cnt[d], 1ull);
             atomicAdd(&H->y_w[d], wgt);
             atomicAdd(&H->y_r[d], (unsigned long long)r);
         } else {
-            unsigned int i = atomicAdd(&H->n_yo, 1u);
+            const unsigned int i = atomicAdd(&H->n_yo, 1u);
             yo[i] = Over{d, wgt, (unsigned long long)r};
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SB; i += blockDim.x)
+        if (s_cnt[i]) {
+            atomicAdd(&H->y_cnt[i], s_cnt[i]);
+            atomicAdd(&H->y_w[i], s_w[i]);
+            atomicAdd(&H->y_r[i], s_r[i]);
+        }
 }
 
 __global__ void hist_z_kernel(int64_t nz, const int32_t* deg_sz, DevHist* H, Over* zo) {
+    __shared__ unsigned long long s_cnt[SB];
+    for (int i = threadIdx.x; i < SB; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nz;
          c += (int64_t)gridDim.x * blockDim.x) {
         const long long d = deg_sz[c];
-        if (d <= HMAX) {
+        if (d < SB) {
+            atomicAdd(&s_cnt[d], 1ull);
+        } else if (d <= HMAX) {
             atomicAdd(&H->z_cnt[d], 1ull);
         } else {
-            unsigned int i = atomicAdd(&H->n_zo, 1u);
+            const unsigned int i = atomicAdd(&H->n_zo, 1u);
             zo[i] = Over{d, 0, 0};
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SB; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(&H->z_cnt[i], s_cnt[i]);
 }
 
 // Cumulative index over degrees: values with degree <= delta.
@@ -257,16 +261,16 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
     Over* zo = ws.get<Over>(g.nz + 1);
     JP_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(DevHist), st));
     if (g.nx) {
-        hist_x_kernel<<<grid_for(g.nx, 256, 152 * 16), 256, 0, st>>>(g.nx, g.rxoff, g.rycol,
-                                                                        g.deg_sy, H, xo);
+        if (!g.xsum) throw Error{JP_EINVAL, "threshold selection needs the per-x candidate sums"};
+        hist_x_kernel<<<grid_for(g.nx, 256, 152 * 4), 256, 0, st>>>(g.nx, g.rxoff, g.xsum, H, xo);
         JP_CHECK_LAUNCH();
     }
     if (g.ny) {
-        hist_y_kernel<<<grid_for(g.ny, 256, 152 * 16), 256, 0, st>>>(g.ny, g.deg_ry, g.deg_sy, H, yo);
+        hist_y_kernel<<<grid_for(g.ny, 256, 152 * 4), 256, 0, st>>>(g.ny, g.deg_ry, g.deg_sy, H, yo);
         JP_CHECK_LAUNCH();
     }
     if (!g.self && g.nz) {
-        hist_z_kernel<<<grid_for(g.nz, 256, 152 * 16), 256, 0, st>>>(g.nz, g.deg_sz, H, zo);
+        hist_z_kernel<<<grid_for(g.nz, 256, 152 * 4), 256, 0, st>>>(g.nz, g.deg_sz, H, zo);
         JP_CHECK_LAUNCH();
     }
     std::vector<DevHist> hh(1);

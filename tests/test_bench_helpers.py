@@ -19,6 +19,45 @@ def test_cpu_sample_takes_a_prefix_of_x_by_candidates():
     assert (lo, hi, k, c, nx, tot) == (0, 1, 2, 8.0, 4, 14.0)
 
 
+def test_stratified_rows_take_every_kth_by_candidates_with_the_largest():
+    cand = np.array([5.0, 100.0, 1.0, 7.0, 30.0, 2.0, 9.0, 3.0])
+    rows, k = bench.stratified_rows(cand, cand.sum() / 4)
+    # decreasing order: 1 (100), 4 (30), 6 (9), 3 (7), 0 (5), 7 (3), 5 (2), 2 (1): every 4th
+    assert k == 4 and rows.tolist() == [0, 1]
+    rows, k = bench.stratified_rows(cand, 1e9)
+    assert k == 1 and rows.tolist() == list(range(8))
+
+
+def test_split_rows_and_sub_csr():
+    cand = np.array([4.0, 4.0, 4.0, 4.0, 8.0, 8.0])
+    groups = bench.split_rows(np.arange(6), cand, 2)
+    assert [g.tolist() for g in groups] == [[0, 1, 2, 3], [4, 5]]
+    off = np.array([0, 2, 3, 6], np.int64)
+    y = np.array([10, 11, 20, 30, 31, 32], np.int32)
+    so, sy = bench.sub_csr(off, y, np.array([2, 0]))
+    assert so.tolist() == [0, 3, 5] and sy.tolist() == [30, 31, 32, 10, 11]
+
+
+def test_oracle_rows_single_and_pool_count_the_distinct_pairs(oracle_mod):
+    from paper_2002_12459_gb300 import workloads as W
+    rng = np.random.default_rng(4)
+    rx, ry = W.random_small_relation(rng, 4000, 300, 120, -50, 9, 0.8)
+    ox, oz = oracle_mod.two_path(rx, ry)
+    one = bench.OracleRows(rx, ry, 1)
+    n, secs = one.run(np.arange(len(one.ux)))
+    assert n == len(ox) and secs >= 0
+    # candidates per x are sum_{y in R[x]} deg(y)
+    ux, cand = bench.candidate_counts(rx, ry)
+    assert np.array_equal(one.ux, ux) and np.array_equal(one.cand, cand)
+    rows, _ = bench.stratified_rows(one.cand, one.cand.sum() / 5)
+    want = sum(int((ox == one.ux[r]).sum()) for r in rows)
+    two = bench.OracleRows(rx, ry, 2)
+    try:
+        assert two.run(rows)[0] == want == one.run(rows)[0]
+    finally:
+        two.close()
+
+
 def _stats(**kw):
     st = {"out_count": 1000, "u": 256, "v": 128, "w": 512, "dom_x": 10, "k": 2,
           "light_cand": [100, 0, 0, 50, 0, 0, 25, 0], "light_x": [4, 0, 0, 2, 0, 0, 1, 0],
