@@ -465,9 +465,25 @@ def run_ours(args, rank, world, local_rank):
     # steps (same workspace and allocator state as the steps it is compared with)
     e2e = None
     if rank == 0 and not args.no_e2e:
+        # host input columns in, the result written by the output kernel straight into
+        # pinned host columns (jp_two_path_into): every byte crosses the host link
         hrx = torch.from_numpy(rx).pin_memory()
         hry = torch.from_numpy(ry).pin_memory()
         cols = [torch.empty(out + 1, dtype=torch.int32, pin_memory=True) for _ in range(2)]
+        times = []
+        n = 0
+        for i in range(1 + args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n = ctx.two_path_into(hrx, hry, cols[0], cols[1])
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        k = len(times)
+        e2e = {"value": out / (sum(times) / k), "unit": UNIT, "api": "jp_two_path_into",
+               "h2d_bytes_per_step": int(8 * len(rx)), "d2h_bytes_per_step": int(8 * out),
+               "ms_per_step": 1e3 * sum(times) / k, "count_equal": n == out}
+        # the same through jp_two_path + jp_result_to_host (a device result, then copied)
         times, split = [], {}
         for i in range(1 + args.e2e_steps):
             torch.cuda.synchronize()
@@ -477,11 +493,10 @@ def run_ours(args, rank, world, local_rank):
             if i > 0:
                 times.append(time.perf_counter() - t0)
             del gx, gz
-        k = len(times)
-        e2e = {"value": out / (sum(times) / k), "unit": UNIT,
-               "h2d_bytes_per_step": int(8 * len(rx)), "d2h_bytes_per_step": int(8 * out),
-               "ms_per_step": 1e3 * sum(times) / k,
-               "ms_split": {n: round(1e3 * v / k, 2) for n, v in split.items()}}
+        e2e["via_device_result"] = {"ms_per_step": 1e3 * sum(times) / len(times),
+                                    "ms_split": {nm: round(1e3 * v / len(times), 2)
+                                                 for nm, v in split.items()}}
+        del cols, hrx, hry
 
     # the same query at the learned thresholds (the shipped predictor), timed
     # the same way, against the cost-model thresholds above
@@ -521,6 +536,20 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
     if rank != 0:
         return None
+    extra = None
+    if not args.no_extra:
+        extra = {}
+        for name, fn in (("two_path_uniform_20k", lambda: run_uniform(args)),
+                         ("star3_2m", lambda: run_star(args, "star3_2m"))):
+            try:
+                extra[name] = fn()
+            except Exception as e:     # reported, never hidden
+                extra[name] = {"error": f"{type(e).__name__}: {e}"}
+        if "star3_2m" in extra and "metric" in extra["star3_2m"]:
+            r = extra["star3_2m"]
+            extra["star3_2m"] = {k: r[k] for k in ("value", "unit", "ms_per_step", "steps", "config",
+                                                   "roofline", "kernel_rooflines", "cpu_baseline",
+                                                   "parity", "gpu_launches")}
     return {
         "metric": METRIC, "value": world * out / (max_ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
@@ -538,21 +567,23 @@ def run_ours(args, rank, world, local_rank):
                    "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
         "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "parity": parity, "learned_vs_cost_model": learned,
+        "extra_workloads": extra,
     }
 
 
 # ----------------------------------------------------------------- star workload
-def run_star(args):
+def run_star(args, workload=None):
     """Star Q*_3 on the 3 x 2M workload (single GPU, rank 0)."""
     import torch
     from paper_2002_12459_gb300 import build, jp
     from paper_2002_12459_gb300 import workloads as W
 
     build.build()
+    workload = workload or args.workload
     t = time.time()
-    rels = W.make(args.workload)
-    wl = W.WORKLOADS[args.workload]
-    log(f"[bench] workload {args.workload}: {len(rels)} x {len(rels[0][0])} tuples in {time.time() - t:.1f}s")
+    rels = W.make(workload)
+    wl = W.WORKLOADS[workload]
+    log(f"[bench] workload {workload}: {len(rels)} x {len(rels[0][0])} tuples in {time.time() - t:.1f}s")
     drels = [(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()) for x, y in rels]
     ctx = jp.Context(0)
     tensor_peaks = ctx.measure_peaks()
@@ -606,15 +637,15 @@ def run_star(args):
     base = None
     if not args.no_cpu:
         t = time.perf_counter()
-        lo2, hi2 = int(x1[0]), int(x1[min(len(x1) - 1, 250)])
+        lo2, hi2 = int(x1[0]), int(x1[min(len(x1) - 1, 1000)])
         n = len(oracle.star(rels, x_lo=lo2, x_hi=hi2)[0])
         secs = time.perf_counter() - t
         base = {"value": n / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": (f"x1 values {lo2}..{hi2} (251 of {len(x1)}), single-threaded C oracle "
+                "sample": (f"x1 values {lo2}..{hi2} (1001 of {len(x1)}), single-threaded C oracle "
                            f"incl. its sort of the three relations; {n} distinct triples in {secs:.2f}s")}
     peaks, kind = load_peaks()
     peaks.update(tensor_peaks)
-    rl, rl_all = roofline(st, peaks, kind, slot_ms, args.workload)
+    rl, rl_all = roofline(st, peaks, kind, slot_ms, workload)
     launches = sum(s_["kernel_launches"] for s_ in stats)
     ctx.close()
     return {
@@ -622,7 +653,7 @@ def run_star(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_tuples_per_relation": wl["n"], "k": 3,
+        "config": {"workload": workload, "n_tuples_per_relation": wl["n"], "k": 3,
                    "dom_x": wl["dom_x"], "dom_y": wl["dom_y"], "gamma_y": wl["gamma_y"],
                    "seed": wl["seed"], "query": "star Q*_3(x1,x2,x3)=R1(x1,y),R2(x2,y),R3(x3,y)",
                    "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
@@ -633,6 +664,57 @@ def run_star(args):
         "e2e": None, "e2e_note": "not measured: the result is 144 GB, beyond a host copy per step",
         "gpu_launches": launches, "clocks": clocks, "parity": parity,
     }
+
+
+def run_uniform(args, workload="two_path_uniform_20k", delta=141):
+    """The small two-path workload at fixed thresholds floor(sqrt(N)): timed on the GPU, the
+    whole output compared with the oracle, and the oracle timed on one host core."""
+    import torch
+    from paper_2002_12459_gb300 import build, jp
+    import oracle
+
+    build.build()
+    rx, ry, wl = make_workload(workload)
+    dx, dy = torch.from_numpy(rx).cuda(), torch.from_numpy(ry).cuda()
+    ctx = jp.Context(0)
+    ctx.set_threshold("fixed", delta, delta)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ox, oz = ctx.two_path(dx, dy)
+        torch.cuda.synchronize()
+    steps = max(args.steps, 20)
+    ms = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(ctx.stream)
+        ox, oz = ctx.two_path(dx, dy)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    st = ctx.stats()
+    ctx.close()
+    oracle.build()
+    t = time.perf_counter()
+    wx, wz = oracle.two_path(rx, ry)
+    secs = time.perf_counter() - t
+    ok = np.array_equal(ox.cpu().numpy(), wx) and np.array_equal(oz.cpu().numpy(), wz)
+    mean_ms = sum(ms) / len(ms)
+    out = st["out_count"]
+    return {"workload": workload, "value": out / (mean_ms * 1e-3), "unit": UNIT,
+            "ms_per_step": mean_ms, "steps": steps,
+            "config": {"n_tuples": wl["n"], "dom_x": wl["dom_x"], "dom_y": wl["dom_y"],
+                       "seed": wl["seed"], "threshold_mode": "fixed", "delta1": delta,
+                       "delta2": delta, "u": st["u"], "v": st["v"], "out_count": out,
+                       "light_candidates": st["light_candidates"],
+                       "pass_ms": {k: round(v, 4) for k, v in enumerate(st["ms_pass"]) if v > 0}},
+            "parity": {"pairs_checked": int(len(wx)), "bit_exact": bool(ok)},
+            "cpu_baseline": {"value": len(wx) / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the whole relation, single-threaded C oracle: {len(wx)} "
+                                       f"distinct pairs in {secs:.3f}s"},
+            "note": "a tiny query: the time is the pipeline's launches and host synchronisations"}
 
 
 # ----------------------------------------------------------------- set similarity join
@@ -815,6 +897,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the uniform 20k and star k = 3 workloads reported beside the main one")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip timing the query at the shipped predictor's thresholds")
     ap.add_argument("--ref-cand", type=float, default=4.0e8,

@@ -180,6 +180,18 @@ int jp_set_stream(jp_ctx* ctx, void* stream);
  * distinct (x, z) pairs, k = 2.  R->n + S->n must stay below 2^31. */
 int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out);
 
+/* The two-path query of jp_two_path written into caller-owned columns: out_x and out_z hold
+ * cap entries each and may be device memory of the context's device or host memory the GPU
+ * can write (pinned with cudaHostAlloc or cudaHostRegister, or any host memory on a system
+ * whose GPU accesses pageable memory).  The output kernel writes host columns directly over
+ * the host link: no device copy of the result is made.  *count (host) receives |OUT|; when it
+ * exceeds cap nothing is written, JP_EOVERFLOW is returned and *count keeps |OUT| so the
+ * caller can retry with larger buffers (any other failure leaves *count = 0).  Inputs,
+ * thresholds and errors as jp_two_path; JP_EINVAL when a buffer is not writable by the GPU.
+ * The call returns when the columns are written. */
+int jp_two_path_into(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int32_t* out_x, int32_t* out_z,
+                     int64_t cap, int64_t* count);
+
 /* Measured dense tensor rates of this GPU, the denominators of the heavy product's roofline:
  * *fp8_tflops from tcgen05 kind::f8f6f4 MMAs of the product's 128x256x32 shape on operands in
  * shared memory (one CTA per SM, no loads), *int8_mma_sync_tflops from the legacy

@@ -181,6 +181,35 @@ struct BatchArgs {
     int64_t* out_off;        // host, nq + 1
 };
 
+// Caller-owned output columns (jp_two_path_into): device pointers, or host
+// memory the kernels can write (pinned, or any host memory on a device with
+// pageable memory access).
+struct ExtOut {
+    int32_t* x;
+    int32_t* z;
+    int64_t cap;
+    int64_t* count;          // host: |OUT|
+};
+
+// The address kernels use for a caller's output buffer, or null when the GPU
+// cannot write it.
+int32_t* kernel_ptr(jp_ctx* ctx, int32_t* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return a.device == ctx->device ? p : nullptr;
+    if (a.type == cudaMemoryTypeHost) return reinterpret_cast<int32_t*>(a.devicePointer);
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return pageable ? p : nullptr;
+}
+
 // The two-path pipeline.  With a batch, R holds the queries' tuples one after
 // another (batch->qoff) and is a self-join per query; its values are first
 // encoded to (query, value) ids, and the output maps them back.
@@ -190,7 +219,7 @@ struct BatchArgs {
 // answers the reduced query into the workspace, and the result is the pairs of
 // T found in that output.
 int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
-                 const BatchArgs* batch, const jp_rel* T = nullptr) {
+                 const BatchArgs* batch, const jp_rel* T = nullptr, const ExtOut* ext = nullptr) {
     if (!ctx) return JP_EINVAL;
     if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
     std::memset(out, 0, sizeof(*out));
@@ -276,7 +305,20 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
             ctx->tm.end(jp::TM_PLACE);
             result_count = jp::filter_find(fs, qx, qz, count, ctx->ws, st);
         }
-        if (result_count > 0) {
+        if (ext) {
+            *ext->count = result_count;
+            if (result_count > ext->cap)
+                throw jp::Error{JP_EOVERFLOW, "the result has " + std::to_string(result_count) +
+                                                  " pairs, more than the buffers hold"};
+            if (result_count > 0) {
+                int32_t* kx = kernel_ptr(ctx, ext->x);
+                int32_t* kz = kernel_ptr(ctx, ext->z);
+                if (!kx || !kz) throw jp::Error{JP_EINVAL, "an output buffer is not writable by the GPU"};
+                ctx->tm.begin(jp::TM_PLACE);
+                jp::output_write(g, lr, out_off, count, kx, kz, st);
+                ctx->tm.end(jp::TM_PLACE);
+            }
+        } else if (result_count > 0) {
             block_bytes = (size_t)result_count * 2 * sizeof(int32_t) + 512;
             block = ctx->ws.raw_alloc(block_bytes);
             if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
@@ -443,6 +485,19 @@ int jp_set_stream(jp_ctx* ctx, void* stream) {
 
 int jp_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out) {
     return run_two_path(ctx, R, S, out, nullptr);
+}
+
+int jp_two_path_into(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int32_t* out_x, int32_t* out_z,
+                     int64_t cap, int64_t* count) {
+    if (!ctx) return JP_EINVAL;
+    if (!count) return fail(ctx, JP_EINVAL, "count is NULL");
+    *count = 0;
+    if (cap < 0 || (cap > 0 && (!out_x || !out_z))) return fail(ctx, JP_EINVAL, "bad output buffers");
+    jp_result res;
+    const ExtOut ext{out_x, out_z, cap, count};
+    const int rc = run_two_path(ctx, R, S, &res, nullptr, nullptr, &ext);
+    if (rc != JP_OK && !(rc == JP_EOVERFLOW && *count > cap)) *count = 0;
+    return rc;
 }
 
 int jp_two_path_batch(jp_ctx* ctx, const jp_rel* all, int32_t nq, const int64_t* qoff,

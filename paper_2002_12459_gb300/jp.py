@@ -97,6 +97,9 @@ def load(path: str = LIB_PATH):
             lib.jp_two_path.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
                                         ctypes.POINTER(jp_result)]
             lib.jp_two_path.restype = i32
+            lib.jp_two_path_into.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel), vp,
+                                             vp, i64, ctypes.POINTER(ctypes.c_int64)]
+            lib.jp_two_path_into.restype = i32
             lib.jp_two_path_batch.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(jp_result),
@@ -241,6 +244,28 @@ class Context:
                                       ctypes.byref(res))
         self._check(rc)
         return self._take(res)
+
+    def two_path_into(self, rx, ry, out_x, out_z, sz=None, sy=None) -> int:
+        """jp_two_path_into: the sorted distinct pairs written into out_x / out_z (int32
+        tensors on this device, or pinned CPU tensors written directly over the host link).
+        Returns the pair count; raises JPError(JP_EOVERFLOW) with ``.count`` set when the
+        buffers are too small."""
+        for t in (out_x, out_z):
+            if t.dtype != self._torch.int32 or not t.is_contiguous():
+                raise TypeError("output columns must be contiguous int32 tensors")
+        R = _rel_of(rx, ry)
+        S = _rel_of(sz, sy) if sz is not None else None
+        cnt = ctypes.c_int64(0)
+        cap = min(out_x.numel(), out_z.numel())
+        with self._torch.cuda.stream(self.stream):
+            rc = self.lib.jp_two_path_into(self.h, ctypes.byref(R), ctypes.byref(S) if S else None,
+                                           ctypes.c_void_p(out_x.data_ptr()),
+                                           ctypes.c_void_p(out_z.data_ptr()), cap, ctypes.byref(cnt))
+        if rc != JP_OK:
+            err = JPError(rc, self.lib.jp_last_error(self.h).decode())
+            err.count = cnt.value
+            raise err
+        return cnt.value
 
     def two_path_filter(self, tx, tz, rx, ry, sz=None, sy=None):
         """Pairs (a, b) of T = (tx, tz) with R(a, y), S(b, y) for some y: sorted, distinct."""

@@ -216,3 +216,43 @@ def test_every_light_class(ctx, oracle_mod, seed):
     # heavy x and heavy y mixed in
     for d1, d2 in [(200, 30), (60, 8), (350, 65)]:
         assert_same(run(ctx, rx, ry, d1=d1, d2=d2), want)
+
+
+def test_two_path_into_device_and_pinned_host_columns(ctx, oracle_mod):
+    # jp_two_path_into writes the sorted distinct pairs into caller-owned columns: device
+    # tensors, or pinned host tensors written by the output kernel over the host link
+    import torch
+    from paper_2002_12459_gb300 import jp
+    rng = np.random.default_rng(77)
+    rx, ry = rand_rel(rng, 5000, 500, 120, -300, 11, skew=0.8)
+    sz, sy = rand_rel(rng, 4000, 400, 130, 50, 0, skew=0.5)
+    for S in (None, (sz, sy)):
+        want = oracle_mod.two_path(rx, ry) if S is None else oracle_mod.two_path(rx, ry, sz, sy)
+        n = len(want[0])
+        for d1, d2 in [(1, 1), (4, 6), (10 ** 6, 10 ** 6)]:
+            ctx.set_threshold("fixed", d1, d2)
+            args = () if S is None else (dev(sz), dev(sy))
+            ox = torch.full((n + 5,), -7, dtype=torch.int32, device="cuda")
+            oz = torch.full((n + 5,), -7, dtype=torch.int32, device="cuda")
+            assert ctx.two_path_into(dev(rx), dev(ry), ox, oz, *args) == n
+            assert np.array_equal(ox[:n].cpu().numpy(), want[0])
+            assert np.array_equal(oz[:n].cpu().numpy(), want[1])
+            assert int(ox[n]) == -7                                # nothing past the result
+            hx = torch.zeros(n, dtype=torch.int32, pin_memory=True)
+            hz = torch.zeros(n, dtype=torch.int32, pin_memory=True)
+            hrx = torch.from_numpy(np.ascontiguousarray(rx, np.int32)).pin_memory()
+            hry = torch.from_numpy(np.ascontiguousarray(ry, np.int32)).pin_memory()
+            hargs = () if S is None else (torch.from_numpy(sz.astype(np.int32)),
+                                          torch.from_numpy(sy.astype(np.int32)))
+            assert ctx.two_path_into(hrx, hry, hx, hz, *hargs) == n
+            assert np.array_equal(hx.numpy(), want[0]) and np.array_equal(hz.numpy(), want[1])
+    # buffers one pair short: JP_EOVERFLOW, the needed size reported, nothing written
+    ctx.set_threshold("fixed", 4, 6)
+    want = oracle_mod.two_path(rx, ry)
+    n = len(want[0])
+    ox = torch.full((n - 1,), -7, dtype=torch.int32, device="cuda")
+    oz = torch.full((n - 1,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(jp.JPError, match="EOVERFLOW") as ei:
+        ctx.two_path_into(dev(rx), dev(ry), ox, oz)
+    assert ei.value.count == n
+    assert bool((ox == -7).all()) and bool((oz == -7).all())
