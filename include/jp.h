@@ -271,6 +271,22 @@ int jp_set_count_chunk(jp_ctx* ctx, int64_t candidates);
  * or more tuples), the k = 3 algorithm runs on (R1, R2, it), and the ids are expanded. */
 int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out);
 
+/* Batch of star queries Q*_3 (Section 3.2) in one pass of the star pipeline: query q is
+ * Q*_3(R1_q, R2_q, R3_q).  Every x_i and every y is tagged with its query and
+ * dictionary-encoded (y over the three relations together), so the batch is the single star
+ * query of the tagged union: no witness joins tuples of two queries.
+ *   rels     three relations; relation i holds the queries' tuples one after another;
+ *   qoff     host, 3 x (nq + 1) entries: query q's tuples of relation i are
+ *            [qoff[i (nq+1) + q], qoff[i (nq+1) + q + 1]); each row starts at 0, ends at
+ *            rels[i].n and does not decrease (empty queries are allowed);
+ *   out      one result (k = 3) holding the queries' sorted distinct triples, query after
+ *            query;
+ *   out_off  host, nq + 1 entries, receives where each query's triples start.
+ * Thresholds by the context's mode for the union.  Errors as jp_star; JP_EINVAL for bad
+ * offsets. */
+int jp_star_batch(jp_ctx* ctx, int32_t nq, const jp_rel* rels, const int64_t* qoff,
+                  jp_result* out, int64_t* out_off);
+
 /* Statistics of the last successful query. */
 int jp_get_stats(const jp_ctx* ctx, jp_stats* stats);
 

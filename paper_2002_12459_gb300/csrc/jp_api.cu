@@ -806,6 +806,122 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
     }
 }
 
+int jp_star_batch(jp_ctx* ctx, int32_t nq, const jp_rel* rels, const int64_t* qoff, jp_result* out,
+                  int64_t* out_off) {
+    if (!ctx) return JP_EINVAL;
+    if (!out) return fail(ctx, JP_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->k = 3;
+    if (!rels || !qoff || !out_off) return fail(ctx, JP_EINVAL, "NULL argument");
+    if (nq < 1) return fail(ctx, JP_EINVAL, "a batch needs at least one query");
+    for (int i = 0; i < 3; ++i) {
+        int rc = check_rel(ctx, &rels[i], "rels[i]");
+        if (rc) return rc;
+        const int64_t* qo = qoff + (size_t)i * (nq + 1);
+        if (qo[0] != 0 || qo[nq] != rels[i].n)
+            return fail(ctx, JP_EINVAL, "query offsets must start at 0 and end at the tuple count");
+        for (int32_t q = 0; q < nq; ++q)
+            if (qo[q + 1] < qo[q]) return fail(ctx, JP_EINVAL, "query offsets must not decrease");
+    }
+    if (rels[0].n + rels[1].n + rels[2].n >= ((int64_t)1 << 31))
+        return fail(ctx, JP_EUNSUPPORTED, "the relations together hold 2^31 or more tuples");
+    if (rels[0].n == 0 || rels[1].n == 0 || rels[2].n == 0) {   // no query has a triple
+        for (int32_t q = 0; q <= nq; ++q) out_off[q] = 0;
+        std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+        ctx->have_stats = true;
+        return JP_OK;
+    }
+    const auto t_start = std::chrono::steady_clock::now();
+    void* block = nullptr;
+    size_t block_bytes = 0;
+    try {
+        JP_CUDA_TRY(cudaSetDevice(ctx->device));
+        cudaStream_t st = ctx->stream;
+        ctx->ws.begin();
+        const int64_t launches0 = jp::g_launches;
+        JP_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), st));
+        for (int i = 0; i < jp::TM_SLOTS; ++i) ctx->tm.used[i] = false;
+        ctx->tm.st = st;
+        jp::g_timer = &ctx->tm;
+        ctx->tm.begin(jp::TM_TOTAL);
+        jp_rel rd[3];
+        for (int i = 0; i < 3; ++i) rd[i] = to_device(ctx, &rels[i]);
+        ctx->tm.begin(jp::TM_BUILD);
+        jp::StarBatchIds sb;
+        jp::star_batch_encode(rd, nq, qoff, sb, ctx->ws, st, ctx->hist_host, ctx->d_status);
+        jp::StarOut so;
+        jp::run_star3(sb.rel, ctx->mode, ctx->d1, ctx->d2, so, ctx->ws, st, ctx->d_status,
+                      ctx->hist_host);
+        ctx->tm.end(jp::TM_BUILD);
+        jp::Heavy h;
+        ctx->tm.begin(jp::TM_PACK);
+        jp::heavy_pack(so.g, so.p, h, ctx->ws, st);
+        ctx->tm.end(jp::TM_PACK);
+        jp::heavy_gemm(h, so.p, ctx->d_status, st, nullptr);
+        jp::LightResult lr;
+        jp::light_and_union(so.g, so.p, h, lr, ctx->ws, st, ctx->d_status, ctx->host_scalars);
+        int64_t* oo = ctx->ws.get<int64_t>(so.g.nx + 1);
+        ctx->tm.begin(jp::TM_COUNT);
+        const int64_t count = jp::output_count(so.g, lr, oo, ctx->ws, st, ctx->host_scalars);
+        ctx->tm.end(jp::TM_COUNT);
+        status_check(ctx);
+        int32_t* cols[3] = {nullptr, nullptr, nullptr};
+        if (count > 0) {
+            const size_t col_bytes = ((size_t)count * sizeof(int32_t) + 255) & ~(size_t)255;
+            block_bytes = 3 * col_bytes;
+            block = ctx->ws.raw_alloc(block_bytes);
+            if (!block) throw jp::Error{JP_ENOMEM, "result allocation failed"};
+            for (int i = 0; i < 3; ++i)
+                cols[i] = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(block) + i * col_bytes);
+            ctx->tm.begin(jp::TM_PLACE);
+            jp::output_write_rows(so.g, lr, oo, count, so.row1, so.row2, cols[0], cols[1], cols[2],
+                                  st);
+            ctx->tm.end(jp::TM_PLACE);
+        }
+        jp::star_batch_finish(cols, count, sb, nq, out_off, ctx->ws, st);
+        ctx->tm.end(jp::TM_TOTAL);
+        status_check(ctx);
+        jp::g_timer = nullptr;
+        for (int i = 0; i < 3; ++i) out->col[i] = cols[i];
+        out->count = count;
+        out->_block = block;
+        out->_bytes = block_bytes;
+        jp_stats& s = ctx->stats;
+        std::memset(&s, 0, sizeof(s));
+        s.n_r = so.n_rel[0];
+        s.n_s = so.n_rel[1];
+        s.dom_x = so.nx[0];
+        s.dom_y = so.ny;
+        s.dom_z = so.nx[2];
+        s.out_join = so.out_join;
+        s.out_estimate = so.out_join;
+        s.delta1 = so.d1;
+        s.delta2 = so.d2;
+        s.threshold_mode = ctx->mode;
+        s.u = so.p.u;
+        s.v = so.p.v;
+        s.w = so.p.w;
+        s.light_candidates = lr.candidates;
+        s.out_count = count;
+        s.kernel_launches = jp::g_launches - launches0;
+        for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
+        s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        ctx->have_stats = true;
+        ctx->err.clear();
+        return JP_OK;
+    } catch (const jp::Error& e) {
+        jp::g_timer = nullptr;
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, e.code, e.msg);
+    } catch (const std::bad_alloc&) {
+        jp::g_timer = nullptr;
+        if (block) ctx->ws.raw_free(block, block_bytes);
+        std::memset(out, 0, sizeof(*out));
+        return fail(ctx, JP_ENOMEM, "host allocation failed");
+    }
+}
+
 int jp_set_predictor(jp_ctx* ctx, jp_mlp* model) {
     if (!ctx) return JP_EINVAL;
     ctx->predictor = model;

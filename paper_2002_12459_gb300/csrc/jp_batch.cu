@@ -152,6 +152,141 @@ void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
     }
 }
 
+// ------------------------------------------------------------ star batches
+// nq star queries Q*_3 over (R1_q, R2_q, R3_q): relation i holds the queries'
+// tuples one after another (qoff_i).  Every x_i and every y is tagged with its
+// query and dictionary-encoded: x_i per relation, y over the three relations
+// together, so that the three relations of one query share their y ids and no
+// two queries share any.  Q*_3 of the tagged union is then the union of the
+// queries' answers, each x1 id range holding one query.
+namespace {
+
+__global__ void tag_one_kernel(const int32_t* __restrict__ v, int64_t n,
+                               const int64_t* __restrict__ qoff, int32_t nq, uint64_t* key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = nq;            // last q with qoff[q] <= i
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (qoff[mid] <= i) lo = mid; else hi = mid;
+        }
+        key[i] = ((uint64_t)lo << 32) | ((uint32_t)v[i] ^ BIAS);
+    }
+}
+
+// first output position whose x1 id is at least begin[q] (the output is
+// sorted by x1 id first)
+__global__ void star_offsets_kernel(const int32_t* __restrict__ col0, int64_t count,
+                                    const int32_t* __restrict__ begin, int32_t nq,
+                                    int64_t* __restrict__ off) {
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x) {
+        const int32_t b = begin[q];
+        int64_t lo = 0, hi = count;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (col0[mid] < b) lo = mid + 1; else hi = mid;
+        }
+        off[q] = lo;
+    }
+}
+
+__global__ void map_cols_kernel(int32_t* c0, int32_t* c1, int32_t* c2, int64_t n,
+                                const int32_t* __restrict__ v0, const int32_t* __restrict__ v1,
+                                const int32_t* __restrict__ v2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        c0[i] = v0[c0[i]];
+        c1[i] = v1[c1[i]];
+        c2[i] = v2[c2[i]];
+    }
+}
+
+}  // namespace
+
+void star_batch_encode(const jp_rel* rels, int32_t nq, const int64_t* qoff_host, StarBatchIds& b,
+                       Arena& ws, cudaStream_t st, uint32_t* hist_host, uint32_t* d_status) {
+    int64_t* qoff[3];
+    int64_t ntot = 0;
+    for (int i = 0; i < 3; ++i) {
+        qoff[i] = ws.get<int64_t>((size_t)nq + 1);
+        JP_CUDA_TRY(cudaMemcpyAsync(qoff[i], qoff_host + (size_t)i * (nq + 1),
+                                    ((size_t)nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        ntot += rels[i].n;
+    }
+    // y: the three relations' tagged y together
+    const int64_t m = ntot > 0 ? ntot : 1;
+    uint64_t* ky = ws.get<uint64_t>(m);
+    uint64_t* t0 = ws.get<uint64_t>(m);
+    uint64_t* t1 = ws.get<uint64_t>(m);
+    int64_t at = 0;
+    for (int i = 0; i < 3; ++i) {
+        if (rels[i].n > 0) {
+            tag_one_kernel<<<G(rels[i].n), 256, 0, st>>>(rels[i].y, rels[i].n, qoff[i], nq, ky + at);
+            JP_CHECK_LAUNCH();
+        }
+        at += rels[i].n;
+    }
+    if (ntot > 0)
+        JP_CUDA_TRY(cudaMemcpyAsync(t0, ky, ntot * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    int64_t nyg = 0;
+    uint64_t* uy = sorted_distinct(t0, t1, ntot, &nyg, ws, st, hist_host);
+    uint64_t* kx = (uy == t0) ? t1 : t0;      // free buffer for the x keys
+    at = 0;
+    for (int i = 0; i < 3; ++i) {
+        const int64_t n = rels[i].n;
+        b.rel[i].n = n;
+        int32_t* yg = ws.get<int32_t>(n > 0 ? n : 1);
+        int32_t* xg = ws.get<int32_t>(n > 0 ? n : 1);
+        if (n > 0) {
+            find_kernel<<<G(n), 256, 0, st>>>(uy, nyg, ky + at, n, yg, d_status);
+            JP_CHECK_LAUNCH();
+            tag_one_kernel<<<G(n), 256, 0, st>>>(rels[i].x, n, qoff[i], nq, kx);
+            JP_CHECK_LAUNCH();
+        }
+        // x_i: sorted distinct tagged values -> ids and values
+        uint64_t* s0 = ws.get<uint64_t>(n > 0 ? n : 1);
+        uint64_t* s1 = ws.get<uint64_t>(n > 0 ? n : 1);
+        if (n > 0)
+            JP_CUDA_TRY(cudaMemcpyAsync(s0, kx, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+        int64_t nxg = 0;
+        uint64_t* ux = sorted_distinct(s0, s1, n, &nxg, ws, st, hist_host);
+        b.xorig[i] = ws.get<int32_t>(nxg + 1);
+        if (nxg > 0) {
+            value_kernel<<<G(nxg), 256, 0, st>>>(ux, nxg, b.xorig[i]);
+            JP_CHECK_LAUNCH();
+        }
+        if (n > 0) {
+            find_kernel<<<G(n), 256, 0, st>>>(ux, nxg, kx, n, xg, d_status);
+            JP_CHECK_LAUNCH();
+        }
+        if (i == 0) {
+            b.x1q_begin = ws.get<int32_t>((size_t)nq + 1);
+            query_begin_kernel<<<grid_for((int64_t)nq + 1, 256, 152), 256, 0, st>>>(ux, nxg, nq,
+                                                                                    b.x1q_begin);
+            JP_CHECK_LAUNCH();
+        }
+        b.rel[i].x = xg;
+        b.rel[i].y = yg;
+        at += n;
+    }
+}
+
+void star_batch_finish(int32_t* const* cols, int64_t count, const StarBatchIds& b, int32_t nq,
+                       int64_t* host_offsets, Arena& ws, cudaStream_t st) {
+    int64_t* off = ws.get<int64_t>((size_t)nq + 1);
+    star_offsets_kernel<<<grid_for((int64_t)nq + 1, 256, 152), 256, 0, st>>>(cols[0], count,
+                                                                             b.x1q_begin, nq, off);
+    JP_CHECK_LAUNCH();
+    if (count > 0) {
+        map_cols_kernel<<<G(count), 256, 0, st>>>(cols[0], cols[1], cols[2], count, b.xorig[0],
+                                                  b.xorig[1], b.xorig[2]);
+        JP_CHECK_LAUNCH();
+    }
+    JP_CUDA_TRY(cudaMemcpyAsync(host_offsets, off, ((size_t)nq + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, st));
+    JP_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
 void batch_offsets(const int64_t* out_off, int64_t nx, int64_t count, const BatchIds& b,
                    int32_t nq, int64_t* host_offsets, Arena& ws, cudaStream_t st) {
     int64_t* off = ws.get<int64_t>((size_t)nq + 1);

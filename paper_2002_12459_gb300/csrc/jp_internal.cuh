@@ -163,6 +163,19 @@ struct BatchIds {
 void batch_encode(const int32_t* x, const int32_t* y, int64_t n, int32_t nq,
                   const int64_t* qoff_host, BatchIds& b, Arena& ws, cudaStream_t st,
                   uint32_t* hist_host, uint32_t* d_status);
+// Batches of star queries k = 3 (jp_batch.cu): each relation's x tagged and
+// encoded, y encoded over the three relations together.
+struct StarBatchIds {
+    jp_rel rel[3] = {};               // the relations in global ids
+    int32_t* xorig[3] = {};           // global x_i id -> value
+    int32_t* x1q_begin = nullptr;     // [nq + 1] first global x1 id of every query
+};
+void star_batch_encode(const jp_rel* rels, int32_t nq, const int64_t* qoff_host, StarBatchIds& b,
+                       Arena& ws, cudaStream_t st, uint32_t* hist_host, uint32_t* d_status);
+// Output offset of every query's first triple (host, nq + 1 entries), then the
+// three columns mapped from global ids to values in place.
+void star_batch_finish(int32_t* const* cols, int64_t count, const StarBatchIds& b, int32_t nq,
+                       int64_t* host_offsets, Arena& ws, cudaStream_t st);
 // Output offset of every query's first pair (host, nq + 1 entries).
 void batch_offsets(const int64_t* out_off, int64_t nx, int64_t count, const BatchIds& b,
                    int32_t nq, int64_t* host_offsets, Arena& ws, cudaStream_t st);

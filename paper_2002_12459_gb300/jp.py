@@ -118,6 +118,10 @@ def load(path: str = LIB_PATH):
             dp = ctypes.POINTER(ctypes.c_double)
             lib.jp_measure_peaks.argtypes = [vp, dp, dp]
             lib.jp_measure_peaks.restype = i32
+            lib.jp_star_batch.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(jp_rel),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(jp_result),
+                                          ctypes.POINTER(ctypes.c_int64)]
+            lib.jp_star_batch.restype = i32
             lib.jp_star.argtypes = [vp, i32, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_result)]
             lib.jp_star.restype = i32
             lib.jp_get_stats.argtypes = [vp, ctypes.POINTER(jp_stats)]
@@ -343,6 +347,36 @@ class Context:
             rc = self.lib.jp_star(self.h, k, arr, ctypes.byref(res))
         self._check(rc)
         return self._take(res)
+
+    def star_batch(self, queries):
+        """jp_star_batch: ``queries`` is a list of star queries, each three relations
+        ``[(x1, y1), (x2, y2), (x3, y3)]`` of int32 tensors (all on this device, or all on the
+        host).  Returns (c0, c1, c2, out_off): the queries' sorted distinct triples one after
+        another and, as a numpy int64 array of nq + 1 entries, where each query's start."""
+        import numpy as np
+        torch = self._torch
+        nq = len(queries)
+        qoff = np.zeros((3, nq + 1), np.int64)
+        cols = []
+        for i in range(3):
+            xs = [q[i][0] for q in queries]
+            ys = [q[i][1] for q in queries]
+            qoff[i, 1:] = np.cumsum([x.numel() for x in xs])
+            cols.append((torch.cat(xs).contiguous(), torch.cat(ys).contiguous()))
+        rels = (jp_rel * 3)(*[_rel_of(x, y) for x, y in cols])
+        out_off = np.zeros(nq + 1, np.int64)
+        res = jp_result()
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        with torch.cuda.stream(self.stream):
+            rc = self.lib.jp_star_batch(self.h, nq, rels, qoff.ctypes.data_as(i64p),
+                                        ctypes.byref(res), out_off.ctypes.data_as(i64p))
+        self._check(rc)
+        if res.count == 0:
+            self.lib.jp_result_free(self.h, ctypes.byref(res))
+            e = torch.empty(0, dtype=torch.int32, device=self.device)
+            return e, e.clone(), e.clone(), out_off
+        c0, c1, c2 = self._take(res)
+        return c0, c1, c2, out_off
 
     def two_path_host(self, rx, ry, out_cols=None, timings=None):
         """End-to-end call with HOST input columns (pinned torch CPU tensors).

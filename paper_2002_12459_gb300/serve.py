@@ -6,8 +6,8 @@ servers answer the same trace on one GPU:
 
   batched   whenever the GPU is free, every two-path request that has
             arrived and waits is answered by one jp_two_path_batch call (the
-            whole batch in one pass of the pipeline, each pass one launch);
-            waiting star requests follow one jp_star call each;
+            whole batch in one pass of the pipeline, each pass one launch),
+            and every waiting star request by one jp_star_batch call;
   single    one request at a time, in arrival order.
 
 A request is received when it arrives: its columns are copied to the
@@ -101,8 +101,11 @@ def _receive(req, torch):
                         for x, y in req["rels"]]
 
 
-def serve(ctx, reqs, times, mode, max_batch_tuples=3e7, log=None):
-    """Run the trace; returns per-request latency (s), output tuples and GPU busy time."""
+def serve(ctx, reqs, times, mode, max_batch_tuples=3e7, log=None, keep=None):
+    """Run the trace; returns per-request latency (s), output tuples and GPU busy time.
+
+    With ``keep`` (a dict), every request's answer is stored there as numpy columns.
+    """
     import torch
     clock = _Clock()
     n = len(reqs)
@@ -113,6 +116,11 @@ def serve(ctx, reqs, times, mode, max_batch_tuples=3e7, log=None):
     busy = 0.0
     batches = 0
     done = 0
+
+    def kept(i, cols):
+        if keep is not None:
+            keep[i] = tuple(c.cpu().numpy() for c in cols)
+
     while done < n:
         now = clock.now()
         while nxt < n and times[nxt] <= now:
@@ -126,18 +134,20 @@ def serve(ctx, reqs, times, mode, max_batch_tuples=3e7, log=None):
         if mode == "single":
             group = [waiting.pop(0)]
         else:
-            group, total = [], 0
-            for i in list(waiting):
-                if reqs[i]["kind"] != "two_path":
-                    continue
-                if group and total + reqs[i]["n"] > max_batch_tuples:
-                    break
-                group.append(i)
-                total += reqs[i]["n"]
-            group += [i for i in waiting if reqs[i]["kind"] == "star"]   # then every waiting star
+            group = []
+            for kind, size in (("two_path", 1), ("star", 3)):
+                total = 0
+                for i in list(waiting):
+                    if reqs[i]["kind"] != kind:
+                        continue
+                    if group and total + size * reqs[i]["n"] > max_batch_tuples:
+                        break
+                    group.append(i)
+                    total += size * reqs[i]["n"]
             for i in group:
                 waiting.remove(i)
         two = [i for i in group if reqs[i]["kind"] == "two_path"]
+        stars = [i for i in group if reqs[i]["kind"] == "star"]
         if mode == "batched" and len(two) > 1:
             xs = torch.cat([reqs[i]["dx"] for i in two])
             ys = torch.cat([reqs[i]["dy"] for i in two])
@@ -149,6 +159,7 @@ def serve(ctx, reqs, times, mode, max_batch_tuples=3e7, log=None):
             for k, i in enumerate(two):
                 outs[i] = off[k + 1] - off[k]
                 lat[i] = t_end - times[i]
+                kept(i, (ox[off[k]:off[k + 1]], oz[off[k]:off[k + 1]]))
             del ox, oz, xs, ys
             batches += 1
         else:
@@ -157,14 +168,26 @@ def serve(ctx, reqs, times, mode, max_batch_tuples=3e7, log=None):
                 torch.cuda.synchronize()
                 outs[i] = ox.numel()
                 lat[i] = clock.now() - times[i]
+                kept(i, (ox, oz))
                 del ox, oz
                 batches += 1
-        for i in group:
-            if reqs[i]["kind"] == "star":
+        if mode == "batched" and len(stars) > 1:
+            c0, c1, c2, off = ctx.star_batch([reqs[i]["drels"] for i in stars])
+            torch.cuda.synchronize()
+            t_end = clock.now()
+            for k, i in enumerate(stars):
+                outs[i] = off[k + 1] - off[k]
+                lat[i] = t_end - times[i]
+                kept(i, tuple(c[off[k]:off[k + 1]] for c in (c0, c1, c2)))
+            del c0, c1, c2
+            batches += 1
+        else:
+            for i in stars:
                 cols = ctx.star(reqs[i]["drels"])
                 torch.cuda.synchronize()
                 outs[i] = cols[0].numel()
                 lat[i] = clock.now() - times[i]
+                kept(i, cols)
                 del cols
                 batches += 1
         for i in group:

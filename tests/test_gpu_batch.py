@@ -141,3 +141,72 @@ def test_bad_offsets_are_rejected(ctx):
         ctx.two_path_batch(x, x, np.array([0, 5, 3, 10]))
     with pytest.raises(jp.JPError, match="EINVAL"):
         ctx.two_path_batch(x, x, np.array([0, 9]))
+
+
+def _star_queries(seed, count):
+    rng = np.random.default_rng(seed)
+    qs = []
+    for q in range(count):
+        n = int(rng.integers(50, 4000))
+        dy = int(rng.integers(5, 120))
+        rels = []
+        for i in range(3):
+            m = 0 if (q == 2 and i == 1) else n + int(rng.integers(-40, 40))   # one query has an empty relation
+            x = rng.integers(-300, 300, max(m, 0)).astype(np.int32)
+            y = (rng.integers(0, dy, max(m, 0)) - dy // 2).astype(np.int32)
+            rels.append((x, y))
+        qs.append(rels)
+    return qs
+
+
+_STAR_WANTS = {}
+
+
+def _star_wants(oracle_mod, seed, qs):
+    if seed not in _STAR_WANTS:
+        _STAR_WANTS[seed] = [oracle_mod.star(rels) if all(len(r[0]) for r in rels)
+                             else tuple(np.empty(0, np.int32) for _ in range(3)) for rels in qs]
+    return _STAR_WANTS[seed]
+
+
+@pytest.mark.parametrize("mode,d1,d2", [("fixed", 1, 1), ("fixed", 4, 3), ("fixed", 10 ** 6, 10 ** 6),
+                                        ("cost_model", 1, 1)])
+def test_star_batch_against_oracle(ctx, oracle_mod, mode, d1, d2):
+    # every slice of the batch equals the oracle's answer for that query alone; the
+    # queries' values overlap, so a witness shared across queries would show up
+    qs = _star_queries(31, 9)
+    wants = _star_wants(oracle_mod, 31, qs)
+    ctx.set_threshold(mode, d1, d2)
+    c0, c1, c2, off = ctx.star_batch([[(dev(x), dev(y)) for x, y in q] for q in qs])
+    g = [c.cpu().numpy() for c in (c0, c1, c2)]
+    assert off[0] == 0 and off[-1] == len(g[0])
+    for q, rels in enumerate(qs):
+        want = wants[q]
+        assert off[q + 1] - off[q] == len(want[0]), q
+        for i in range(3):
+            assert np.array_equal(g[i][off[q]:off[q + 1]], want[i]), (q, i)
+
+
+def test_star_batch_of_one_is_the_star_query(ctx, oracle_mod):
+    import torch
+    qs = _star_queries(5, 1)
+    ctx.set_threshold("fixed", 3, 2)
+    c = ctx.star_batch([[(dev(x), dev(y)) for x, y in qs[0]]])
+    s = ctx.star([(dev(x), dev(y)) for x, y in qs[0]])
+    assert c[3].tolist() == [0, s[0].numel()]
+    for i in range(3):
+        assert torch.equal(c[i], s[i])
+
+
+def test_star_batch_bad_offsets_are_rejected(ctx):
+    from paper_2002_12459_gb300 import jp
+    import ctypes
+    x = dev(np.arange(10))
+    rels = (jp.jp_rel * 3)(*[jp._rel_of(x, x) for _ in range(3)])
+    qoff = np.array([[0, 5, 3, 10]] * 3, np.int64)
+    out_off = np.zeros(4, np.int64)
+    res = jp.jp_result()
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    rc = ctx.lib.jp_star_batch(ctx.h, 3, rels, qoff.ctypes.data_as(i64p), ctypes.byref(res),
+                               out_off.ctypes.data_as(i64p))
+    assert rc == jp.JP_EINVAL
