@@ -123,6 +123,7 @@ typedef struct {
                                   sorted in one pass each (ms_pass[13..15] sum their phases) */
     int64_t count_light_pairs; /* jp_two_path_counts only: distinct (x, z) among the light candidates
                                   (heavy_pairs: nonzero entries of the heavy product) */
+    int64_t gemm_tile;         /* tile width of the heavy product (128 or 256; 0: no product) */
 } jp_stats;
 
 typedef void* (*jp_alloc_fn)(size_t bytes, void* stream, void* user);
@@ -171,6 +172,15 @@ typedef struct {
 int jp_set_cost_model(jp_ctx* ctx, const jp_cost_model* model);
 /* The context's current constants. */
 int jp_get_cost_model(const jp_ctx* ctx, jp_cost_model* model);
+
+/* Tile of the heavy product (the tcgen05 kernel computes one tile of 128 heavy x by `width`
+ * heavy z per CTA): width 128 or 256, or 0 (auto, the default): 128 when the product has at
+ * most auto_max_tiles tiles of 128 x 256 (small products then spread over more SMs), else 256.
+ * The default crossover comes from the tile autotuner (paper_2002_12459_gb300/tune.py), which
+ * times both widths on products of many shapes.  JP_EINVAL for another width or a negative
+ * count.  jp_two_path_counts always uses width 256. */
+int jp_set_gemm_tile(jp_ctx* ctx, int width, int64_t auto_max_tiles);
+int jp_get_gemm_tile(const jp_ctx* ctx, int* width, int64_t* auto_max_tiles);
 
 /* Change the stream of subsequent calls. */
 int jp_set_stream(jp_ctx* ctx, void* stream);

@@ -25,6 +25,9 @@ struct jp_ctx {
     jp_mlp* predictor = nullptr;       // borrowed model for JP_LEARNED
     int64_t count_chunk = (int64_t)1 << 27;   // light candidates per pass of jp_two_path_counts
     jp_cost_model cost = jp::default_cost_model();   // Algorithm 3's constants
+    int gemm_width = 0;                 // product tile width: 0 auto, 128 or 256
+    int64_t gemm_auto_tiles = 32;       // auto: narrow tiles up to this many 128 x 256 tiles
+                                        // (the crossover the tile autotuner measured on GB300)
 };
 
 namespace jp {
@@ -281,6 +284,7 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         jp::Heavy h;
         ctx->tm.begin(jp::TM_PACK);
         jp::heavy_pack(g, p, h, ctx->ws, st);
+        h.tbn = jp::pick_tile(h, ctx->gemm_width, ctx->gemm_auto_tiles);
         ctx->tm.end(jp::TM_PACK);
         const int2* tiles = batch ? jp::batch_tile_ranges(p, h, bid.xq_begin, bid.yq_begin,
                                                           batch->nq, ctx->ws, st)
@@ -365,6 +369,7 @@ int run_two_path(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, jp_result* out,
         s.filter_pairs = T ? fs.nt : 0;
         s.filter_query_out = T ? count : 0;
         s.kernel_launches = jp::g_launches - launches0;
+        s.gemm_tile = h.present ? h.tbn : 0;
         for (int q = 0; q < 8; ++q) {
             s.light_x[q] = lr.class_x[q];
             s.light_cand[q] = lr.class_cand[q];
@@ -473,6 +478,22 @@ int jp_set_cost_model(jp_ctx* ctx, const jp_cost_model* model) {
 int jp_get_cost_model(const jp_ctx* ctx, jp_cost_model* model) {
     if (!ctx || !model) return JP_EINVAL;
     *model = ctx->cost;
+    return JP_OK;
+}
+
+int jp_set_gemm_tile(jp_ctx* ctx, int width, int64_t auto_max_tiles) {
+    if (!ctx) return JP_EINVAL;
+    if (width != 0 && width != 128 && width != 256) return fail(ctx, JP_EINVAL, "tile width must be 0, 128 or 256");
+    if (auto_max_tiles < 0) return fail(ctx, JP_EINVAL, "auto_max_tiles must be >= 0");
+    ctx->gemm_width = width;
+    ctx->gemm_auto_tiles = auto_max_tiles;
+    return JP_OK;
+}
+
+int jp_get_gemm_tile(const jp_ctx* ctx, int* width, int64_t* auto_max_tiles) {
+    if (!ctx || !width || !auto_max_tiles) return JP_EINVAL;
+    *width = ctx->gemm_width;
+    *auto_max_tiles = ctx->gemm_auto_tiles;
     return JP_OK;
 }
 
@@ -619,6 +640,7 @@ int jp_two_path_counts(jp_ctx* ctx, const jp_rel* R, const jp_rel* S, int64_t c_
         s.out_count = cr.n;
         s.learned_judged = judged;
         s.kernel_launches = jp::g_launches - launches0;
+        s.gemm_tile = h.present ? h.tbn : 0;
         for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
         s.ms_pass[13] = cr.ms_fill;
         s.ms_pass[14] = cr.ms_sort;
@@ -731,6 +753,7 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         jp::Heavy h;
         ctx->tm.begin(jp::TM_PACK);
         jp::heavy_pack(so.g, so.p, h, ctx->ws, st);
+        h.tbn = jp::pick_tile(h, ctx->gemm_width, ctx->gemm_auto_tiles);
         ctx->tm.end(jp::TM_PACK);
         jp::heavy_gemm(h, so.p, ctx->d_status, st, nullptr);
         jp::LightResult lr;
@@ -783,6 +806,7 @@ int jp_star(jp_ctx* ctx, int k, const jp_rel* rels, jp_result* out) {
         s.light_candidates = lr.candidates;
         s.out_count = count;
         s.kernel_launches = jp::g_launches - launches0;
+        s.gemm_tile = h.present ? h.tbn : 0;
         for (int q = 0; q < 8; ++q) {
             s.light_x[q] = lr.class_x[q];
             s.light_cand[q] = lr.class_cand[q];
@@ -856,6 +880,7 @@ int jp_star_batch(jp_ctx* ctx, int32_t nq, const jp_rel* rels, const int64_t* qo
         jp::Heavy h;
         ctx->tm.begin(jp::TM_PACK);
         jp::heavy_pack(so.g, so.p, h, ctx->ws, st);
+        h.tbn = jp::pick_tile(h, ctx->gemm_width, ctx->gemm_auto_tiles);
         ctx->tm.end(jp::TM_PACK);
         jp::heavy_gemm(h, so.p, ctx->d_status, st, nullptr);
         jp::LightResult lr;
@@ -904,6 +929,7 @@ int jp_star_batch(jp_ctx* ctx, int32_t nq, const jp_rel* rels, const int64_t* qo
         s.light_candidates = lr.candidates;
         s.out_count = count;
         s.kernel_launches = jp::g_launches - launches0;
+        s.gemm_tile = h.present ? h.tbn : 0;
         for (int i = 0; i < jp::TM_SLOTS; ++i) s.ms_pass[i] = ctx->tm.ms(i);
         s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         ctx->have_stats = true;

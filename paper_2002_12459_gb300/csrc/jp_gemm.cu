@@ -21,23 +21,29 @@ namespace jp {
 namespace {
 
 constexpr int BM = 128;           // rows of A per tile (heavy x)
-constexpr int BN = 256;           // rows of B per tile (heavy z)
+constexpr int BN = 256;           // rows of B per tile (heavy z), the wide tile; heavy z are
+                                  // padded to a multiple of it, so both tile widths fit
 constexpr int BK = 128;           // bytes (= FP8 elements) of K per stage
 constexpr int STAGES = 4;
 constexpr int GROUP_M = 8;          // row tiles per group of the tile order
 constexpr int A_STAGE = BM * BK;  // 16 KB
-constexpr int B_STAGE = BN * BK;  // 32 KB
-constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
 constexpr int GEMM_THREADS = 192;  // warp 0: TMA, warp 1: MMA + TMEM, warps 2..5: epilogue
-constexpr uint32_t TMEM_COLS = 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per bounded wait
-constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 
-// Instruction descriptor of tcgen05.mma kind::f8f6f4: D = F32 (bits 4-5 = 1),
-// A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Per tile width TBN (rows of B per tile, 128 or 256): the B stage, the stage
+// bytes, the shared memory, the TMEM columns (one FP32 accumulator column per
+// output column) and the instruction descriptor of tcgen05.mma kind::f8f6f4:
+// D = F32 (bits 4-5 = 1), A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major
+// (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <int TBN> struct Tile {
+    static_assert(TBN == 128 || TBN == 256, "tile width");
+    static constexpr int B_STAGE = TBN * BK;
+    static constexpr int STAGE_BYTES = A_STAGE + B_STAGE;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr uint32_t TMEM_COLS = TBN;
+    static constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) |
+                                      ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -162,23 +168,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// One 128 x 256 output tile per CTA.  K is consumed in BK-byte stages through
+// One 128 x TBN output tile per CTA.  K is consumed in BK-byte stages through
 // a STAGES-deep TMA ring; each stage feeds BK/32 MMAs (K = 32 per FP8 MMA).
 // The epilogue writes one bit per entry (M_ac > 0) into G, or with COUNTS the
 // entries themselves (the witness counts, exact below 2^24) as uint32 into G
 // read as a count matrix of g_stride entries per row.
-template <bool COUNTS>
+template <bool COUNTS, int TBN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     heavy_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, int num_kb, uint32_t* __restrict__ G,
                       int64_t g_stride, uint32_t* status, const int2* __restrict__ tiles, int gx,
                       int gy) {
+    using T = Tile<TBN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * A_STAGE;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * T::STAGE_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* accum = empty + STAGES;
     uint64_t* drain = accum + 1;
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int mi = first_m + in_group % gsz;
     const int nj = in_group / gsz;
     const int m0 = mi * BM;
-    const int n0 = nj * BN;
+    const int n0 = nj * TBN;
     // K blocks of this tile: all of them, or (batches) those of the queries its
     // rows and columns share; none shared: the tile's product is zero, written
     // before any barrier or tensor memory is set up
@@ -212,11 +219,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             if constexpr (COUNTS) {
                 uint4* crow = reinterpret_cast<uint4*>(
                     G + (int64_t)(m0 + (int)threadIdx.x - 64) * g_stride + n0);
-                for (int j = 0; j < BN / 4; ++j) crow[j] = make_uint4(0u, 0u, 0u, 0u);
+                for (int j = 0; j < TBN / 4; ++j) crow[j] = make_uint4(0u, 0u, 0u, 0u);
             } else {
                 uint32_t* grow = G + (int64_t)(m0 + (int)threadIdx.x - 64) * g_stride + (n0 >> 5);
 #pragma unroll
-                for (int j = 0; j < BN / 32; ++j) grow[j] = 0u;
+                for (int j = 0; j < TBN / 32; ++j) grow[j] = 0u;
             }
         }
         return;
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_holder)),
-                     "r"(TMEM_COLS)
+                     "r"(T::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -251,9 +258,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const int s = i % STAGES;
             const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
             if (!mbar_wait(&empty[s], ph ^ 1u, status)) break;
-            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            mbar_arrive_expect_tx(&full[s], T::STAGE_BYTES);
             tma_load_2d(sA + s * A_STAGE, &tmA, &full[s], kb * BK, m0);
-            tma_load_2d(sB + s * B_STAGE, &tmB, &full[s], kb * BK, n0);
+            tma_load_2d(sB + s * T::B_STAGE, &tmB, &full[s], kb * BK, n0);
             ++issued;
         }
         // drain: every issued load has landed before the CTA may exit
@@ -268,10 +275,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             if (!mbar_wait(&full[s], ph, status)) break;
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + s * A_STAGE);
-            const uint32_t b0 = smem_u32(sB + s * B_STAGE);
+            const uint32_t b0 = smem_u32(sB + s * T::B_STAGE);
 #pragma unroll
             for (int k = 0; k < BK / 32; ++k) {
-                mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC,
+                mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), T::IDESC,
                        (i | k) != 0 ? 1u : 0u);
             }
             mma_commit(&empty[s]);
@@ -289,7 +296,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             if constexpr (COUNTS) {
                 uint4* crow = reinterpret_cast<uint4*>(G + (int64_t)row * g_stride + n0);
 #pragma unroll 1
-                for (int j = 0; j < BN / 32; ++j) {
+                for (int j = 0; j < TBN / 32; ++j) {
                     uint32_t r[32];
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
 #pragma unroll
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             } else {
                 uint32_t* grow = G + (int64_t)row * g_stride + (n0 >> 5);
 #pragma unroll 1
-                for (int j = 0; j < BN / 32; ++j) {
+                for (int j = 0; j < TBN / 32; ++j) {
                     uint32_t r[32];
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * 32), r);
                     uint32_t bits = 0;
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
+                     "r"(T::TMEM_COLS)
                      : "memory");
     }
 }
@@ -399,11 +406,12 @@ __global__ void __launch_bounds__(64, 1) fp8_peak_kernel(int iters, uint32_t* st
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
+    using T = Tile<BN>;
     uint8_t* sB = smem + A_STAGE;
-    uint64_t* done = reinterpret_cast<uint64_t*>(smem + A_STAGE + B_STAGE);
+    uint64_t* done = reinterpret_cast<uint64_t*>(smem + A_STAGE + T::B_STAGE);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < (A_STAGE + B_STAGE) / 16; i += blockDim.x)
+    for (int i = threadIdx.x; i < (A_STAGE + T::B_STAGE) / 16; i += blockDim.x)
         reinterpret_cast<int4*>(smem)[i] = make_int4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operands seen by the MMA unit
     if (threadIdx.x == 0) {
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(64, 1) fp8_peak_kernel(int iters, uint32_t* st
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_holder)),
-                     "r"(TMEM_COLS)
+                     "r"(T::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(64, 1) fp8_peak_kernel(int iters, uint32_t* st
         for (int it = 0; it < iters; ++it) {
 #pragma unroll
             for (int k = 0; k < BK / 32; ++k)
-                mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), IDESC,
+                mma_f8(tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), T::IDESC,
                        (it | k) != 0 ? 1u : 0u);
         }
         mma_commit(done);
@@ -437,7 +445,7 @@ __global__ void __launch_bounds__(64, 1) fp8_peak_kernel(int iters, uint32_t* st
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
+                     "r"(T::TMEM_COLS)
                      : "memory");
     }
 }
@@ -494,15 +502,15 @@ __global__ void tile_range_kernel(const int32_t* __restrict__ hx_inv, int64_t u,
                                   const int32_t* __restrict__ hy_inv, int64_t v,
                                   const int32_t* __restrict__ xq_begin,
                                   const int32_t* __restrict__ yq_begin, int32_t nq, int gx,
-                                  int gy, int2* __restrict__ tiles) {
+                                  int gy, int tbn, int2* __restrict__ tiles) {
     const int64_t nt = (int64_t)gx * gy;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t mi = t / gx, nj = t % gx;
-        const int64_t r0 = mi * BM, c0 = nj * BN;
+        const int64_t r0 = mi * BM, c0 = nj * tbn;
         int2 out = make_int2(0, 0);
         if (r0 < u && c0 < w) {
-            const int64_t r1 = min(u, r0 + BM) - 1, c1 = min(w, c0 + BN) - 1;
+            const int64_t r1 = min(u, r0 + BM) - 1, c1 = min(w, c0 + tbn) - 1;
             const int32_t qa = max(query_of(xq_begin, nq, hx_inv[r0]), query_of(xq_begin, nq, hz_inv[c0]));
             const int32_t qb = min(query_of(xq_begin, nq, hx_inv[r1]), query_of(xq_begin, nq, hz_inv[c1]));
             if (qa <= qb) {
@@ -519,7 +527,7 @@ __global__ void tile_range_kernel(const int32_t* __restrict__ hx_inv, int64_t u,
 
 void measure_peaks(int sms, double* fp8_tflops, double* int8_tflops, uint32_t* d_status,
                    Arena& ws, cudaStream_t st) {
-    const size_t smem = (size_t)A_STAGE + B_STAGE + 1024 + 64;
+    const size_t smem = (size_t)A_STAGE + Tile<BN>::B_STAGE + 1024 + 64;
     smem_limit((const void*)fp8_peak_kernel, smem);
     cudaEvent_t e0, e1;
     JP_CUDA_TRY(cudaEventCreate(&e0));
@@ -555,10 +563,10 @@ void measure_peaks(int sms, double* fp8_tflops, double* int8_tflops, uint32_t* d
 int2* batch_tile_ranges(const Partition& p, const Heavy& h, const int32_t* xq_begin,
                         const int32_t* yq_begin, int32_t nq, Arena& ws, cudaStream_t st) {
     if (!h.present) return nullptr;
-    const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
+    const int gx = (int)(h.w_pad / h.tbn), gy = (int)(h.u_pad / BM);
     int2* tiles = ws.get<int2>((size_t)gx * gy);
     tile_range_kernel<<<grid_for((int64_t)gx * gy, 256, 152 * 4), 256, 0, st>>>(
-        p.hx_inv, p.u, p.hz_inv, p.w, p.hy_inv, p.v, xq_begin, yq_begin, nq, gx, gy, tiles);
+        p.hx_inv, p.u, p.hz_inv, p.w, p.hy_inv, p.v, xq_begin, yq_begin, nq, gx, gy, h.tbn, tiles);
     JP_CHECK_LAUNCH();
     return tiles;
 }
@@ -575,6 +583,7 @@ void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStr
     h.w_pad = round_up(p.w, BN);
     h.v_pad = round_up(p.v, BK);
     h.g_stride = h.w_pad / 32;
+    h.tbn = BN;
     h.A = reinterpret_cast<uint8_t*>(ws.carve((size_t)(h.u_pad * h.v_pad)));
     h.B = reinterpret_cast<uint8_t*>(ws.carve((size_t)(h.w_pad * h.v_pad)));
     h.G = ws.get<uint32_t>((size_t)(h.u_pad * h.g_stride));
@@ -588,18 +597,35 @@ void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStr
     JP_CHECK_LAUNCH();
 }
 
+int pick_tile(const Heavy& h, int width, int64_t auto_max_tiles) {
+    if (width == 128 || width == 256) return width;
+    // auto: products with few wide tiles leave SMs idle; narrow tiles double
+    // the CTAs (the crossover is measured by the tile autotuner)
+    const int64_t wide_tiles = (h.w_pad / BN) * (h.u_pad / BM);
+    return wide_tiles <= auto_max_tiles ? 128 : 256;
+}
+
+namespace {
+template <int TBN>
+void launch_gemm(Heavy& h, uint32_t* d_status, cudaStream_t st, const int2* tiles) {
+    using T = Tile<TBN>;
+    CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
+    CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, TBN);
+    smem_limit((const void*)heavy_gemm_kernel<false, TBN>, T::SMEM);
+    const int gx = (int)(h.w_pad / TBN), gy = (int)(h.u_pad / BM);
+    heavy_gemm_kernel<false, TBN><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, T::SMEM, st>>>(
+        ma, mb, (int)(h.v_pad / BK), h.G, h.g_stride, d_status, tiles, gx, gy);
+    JP_CHECK_LAUNCH();
+}
+}  // namespace
+
 void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
                 const int2* tiles) {
     (void)p;
     if (!h.present) return;
-    CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
-    CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
-    smem_limit((const void*)heavy_gemm_kernel<false>, GEMM_SMEM);
-    const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
     tbegin(TM_GEMM);
-    heavy_gemm_kernel<false><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
-        ma, mb, (int)(h.v_pad / BK), h.G, h.g_stride, d_status, tiles, gx, gy);
-    JP_CHECK_LAUNCH();
+    if (h.tbn == 128) launch_gemm<128>(h, d_status, st, tiles);
+    else launch_gemm<BN>(h, d_status, st, tiles);
     tend(TM_GEMM);
 }
 
@@ -607,10 +633,10 @@ void heavy_gemm_counts(const Heavy& h, uint32_t* C, uint32_t* d_status, cudaStre
     if (!h.present) return;
     CUtensorMap ma = make_map(h.A, h.u_pad, h.v_pad, BM);
     CUtensorMap mb = make_map(h.B, h.w_pad, h.v_pad, BN);
-    smem_limit((const void*)heavy_gemm_kernel<true>, GEMM_SMEM);
+    smem_limit((const void*)heavy_gemm_kernel<true, BN>, Tile<BN>::SMEM);
     const int gx = (int)(h.w_pad / BN), gy = (int)(h.u_pad / BM);
     tbegin(TM_GEMM);
-    heavy_gemm_kernel<true><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, GEMM_SMEM, st>>>(
+    heavy_gemm_kernel<true, BN><<<(unsigned)gx * (unsigned)gy, GEMM_THREADS, Tile<BN>::SMEM, st>>>(
         ma, mb, (int)(h.v_pad / BK), C, h.w_pad, d_status, nullptr, gx, gy);
     JP_CHECK_LAUNCH();
     tend(TM_GEMM);

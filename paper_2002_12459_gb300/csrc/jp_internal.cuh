@@ -130,6 +130,7 @@ struct Heavy {
     uint8_t* B = nullptr;       // [w_pad][v_pad]
     uint32_t* G = nullptr;      // [u_pad][g_stride] bit (h,c) = product (h,c) > 0
     int64_t g_stride = 0;       // words per row
+    int tbn = 256;              // product tile width (rows of B per CTA): 128 or 256
     bool present = false;
 };
 
@@ -224,7 +225,11 @@ void build_light_z_lists(const int32_t* syoff, const int32_t* szcol, Partition& 
 
 // Heavy part (jp_gemm.cu)
 void heavy_pack(const Graph& g, const Partition& p, Heavy& h, Arena& ws, cudaStream_t st);
-// tiles: null, or (batches) the K-block range of every tile (batch_tile_ranges).
+// Product tile width for a heavy block: width 128 or 256 as given, or 0
+// (auto): 128 when the block has at most auto_max_tiles tiles of 128 x 256.
+int pick_tile(const Heavy& h, int width, int64_t auto_max_tiles);
+// tiles: null, or (batches) the K-block range of every tile (batch_tile_ranges,
+// computed for h.tbn).
 void heavy_gemm(Heavy& h, const Partition& p, uint32_t* d_status, cudaStream_t st,
                 const int2* tiles = nullptr);
 // The heavy product's entries (witness counts) as uint32 into C[u_pad][w_pad].

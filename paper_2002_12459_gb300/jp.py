@@ -57,7 +57,8 @@ class jp_stats(ctypes.Structure):
                 ("ms_total", ctypes.c_double),
                 ("ms_pass", ctypes.c_double * 16), ("learned_judged", ctypes.c_int64),
                 ("filter_pairs", ctypes.c_int64), ("filter_query_out", ctypes.c_int64),
-                ("count_ranges", ctypes.c_int64), ("count_light_pairs", ctypes.c_int64)]
+                ("count_ranges", ctypes.c_int64), ("count_light_pairs", ctypes.c_int64),
+                ("gemm_tile", ctypes.c_int64)]
 
 
 class jp_cost_model(ctypes.Structure):
@@ -92,6 +93,10 @@ def load(path: str = LIB_PATH):
             lib.jp_set_cost_model.restype = i32
             lib.jp_get_cost_model.argtypes = [vp, ctypes.POINTER(jp_cost_model)]
             lib.jp_get_cost_model.restype = i32
+            lib.jp_set_gemm_tile.argtypes = [vp, i32, i64]
+            lib.jp_set_gemm_tile.restype = i32
+            lib.jp_get_gemm_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]
+            lib.jp_get_gemm_tile.restype = i32
             lib.jp_set_stream.argtypes = [vp, vp]
             lib.jp_set_stream.restype = i32
             lib.jp_two_path.argtypes = [vp, ctypes.POINTER(jp_rel), ctypes.POINTER(jp_rel),
@@ -179,6 +184,11 @@ class Context:
         if rc != JP_OK:
             raise JPError(rc, "jp_create failed")
         self.h = h
+        table = os.path.join(PKG, "predictor", "gemm_tiles.json")
+        if os.path.exists(table):     # the tile autotuner's crossover (tune.py)
+            import json
+            with open(table) as f:
+                self.set_gemm_tile(0, int(json.load(f)["auto_max_tiles"]))
 
     def close(self):
         if getattr(self, "h", None):
@@ -214,6 +224,16 @@ class Context:
                 raise KeyError(k)
             setattr(m, k, float(v))
         self._check(self.lib.jp_set_cost_model(self.h, ctypes.byref(m)))
+
+    def set_gemm_tile(self, width: int = 0, auto_max_tiles: int = 32):
+        """jp_set_gemm_tile: product tile width 128 or 256, or 0 (auto: 128 up to
+        auto_max_tiles tiles of 128 x 256)."""
+        self._check(self.lib.jp_set_gemm_tile(self.h, int(width), int(auto_max_tiles)))
+
+    def gemm_tile(self):
+        w, t = ctypes.c_int(), ctypes.c_int64()
+        self._check(self.lib.jp_get_gemm_tile(self.h, ctypes.byref(w), ctypes.byref(t)))
+        return w.value, t.value
 
     def cost_model(self) -> dict:
         """The context's current Algorithm 3 constants (jp_get_cost_model)."""

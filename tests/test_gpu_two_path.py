@@ -256,3 +256,46 @@ def test_two_path_into_device_and_pinned_host_columns(ctx, oracle_mod):
         ctx.two_path_into(dev(rx), dev(ry), ox, oz)
     assert ei.value.count == n
     assert bool((ox == -7).all()) and bool((oz == -7).all())
+
+
+@pytest.mark.parametrize("width", [128, 256])
+def test_product_tile_widths(ctx, oracle_mod, width):
+    # both tile widths of the tcgen05 product give the oracle's answer: an all-heavy
+    # query (the product alone), a mixed one, R != S, and a batch (per-tile K ranges)
+    rng = np.random.default_rng(width)
+    rx, ry = W.make("two_path_uniform_20k")
+    sx, sy = rand_rel(rng, 6000, 900, 140, -400, 3, skew=0.6)
+    saved = ctx.gemm_tile()
+    ctx.set_gemm_tile(width, 0)
+    try:
+        assert_same(run(ctx, rx, ry, d1=1, d2=1), oracle_mod.two_path(rx, ry))
+        assert ctx.stats()["gemm_tile"] == width
+        assert_same(run(ctx, sx, sy, d1=3, d2=4), oracle_mod.two_path(sx, sy))
+        assert_same(run(ctx, sx, sy, rx[:7000], ry[:7000], d1=2, d2=2),
+                    oracle_mod.two_path(sx, sy, rx[:7000], ry[:7000]))
+        rels = [rand_rel(rng, n, 300, 60, 0, 0, skew=0.5) for n in (2500, 800, 4000)]
+        x = np.concatenate([a for a, _ in rels])
+        y = np.concatenate([b for _, b in rels])
+        qoff = np.concatenate([[0], np.cumsum([len(a) for a, _ in rels])]).astype(np.int64)
+        ctx.set_threshold("fixed", 2, 2)
+        ox, oz, off = ctx.two_path_batch(dev(x), dev(y), qoff)
+        ox, oz = ox.cpu().numpy(), oz.cpu().numpy()
+        for q, (a, b) in enumerate(rels):
+            wx, wz = oracle_mod.two_path(a, b)
+            assert np.array_equal(ox[off[q]:off[q + 1]], wx) and np.array_equal(oz[off[q]:off[q + 1]], wz)
+    finally:
+        ctx.set_gemm_tile(*saved)
+
+
+def test_auto_tile_follows_the_crossover(ctx):
+    rx, ry = W.make("two_path_uniform_20k")
+    saved = ctx.gemm_tile()
+    try:
+        ctx.set_gemm_tile(0, 10 ** 6)          # every product is "small": narrow tiles
+        run(ctx, rx, ry, d1=1, d2=1)
+        assert ctx.stats()["gemm_tile"] == 128
+        ctx.set_gemm_tile(0, 0)                # none is: wide tiles
+        run(ctx, rx, ry, d1=1, d2=1)
+        assert ctx.stats()["gemm_tile"] == 256
+    finally:
+        ctx.set_gemm_tile(*saved)
