@@ -67,23 +67,26 @@ def heavy_bound(x, y, d1, d2):
 
 
 # grid points whose heavy block is beyond these bounds are not run (their time
-# is taken as infinite): operands over 16 GB, or a product over ~2 s
+# is taken as infinite): operands over 16 GB, a product over ~2 s, or light
+# scratch over 64 GB (every heavy x reserves room for its product row: u * u)
 MAX_BLOCK_BYTES = 16e9
 MAX_BLOCK_OPS = 4e15
+MAX_SCRATCH_BYTES = 64e9
 
 
-def sweep(ctx, dx, dy, x, y, log=None):
+def sweep(ctx, dx, dy, x, y, log=None, reps=2):
     import torch
     from paper_2002_12459_gb300 import jp
     times = {}
     for d1 in D1_GRID:
         for d2 in D2_GRID:
             u, v = heavy_bound(x, y, d1, d2)
-            if 2.0 * u * v > MAX_BLOCK_BYTES or 2.0 * u * v * u > MAX_BLOCK_OPS:
+            if (2.0 * u * v > MAX_BLOCK_BYTES or 2.0 * u * v * u > MAX_BLOCK_OPS
+                    or 4.0 * u * u > MAX_SCRATCH_BYTES):
                 times[(d1, d2)] = math.inf
                 continue
             try:
-                times[(d1, d2)] = query_ms(ctx, dx, dy, "fixed", d1, d2)[0]
+                times[(d1, d2)] = query_ms(ctx, dx, dy, "fixed", d1, d2, reps=reps)[0]
             except jp.JPError as e:      # out of device memory at this grid point
                 times[(d1, d2)] = math.inf
                 torch.cuda.empty_cache()
@@ -136,23 +139,48 @@ def draw_specs(count, seed, n_lo, n_hi, max_join, log, workers=None):
     return out
 
 
-def collect(ctx, specs, log):
+def stream_specs(count, seed, n_lo, n_hi, max_join, log, workers=None, first=0):
+    """Like draw_specs, but yields the relations as the spawned workers produce them
+    (in index order), so that drawing overlaps the GPU sweeps of earlier relations."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    done, i = 0, first
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+        while done < count:
+            batch = [(j, seed, n_lo, n_hi, max_join) for j in range(i, i + 4 * workers)]
+            for (j, *_), (spec, x, y) in zip(batch, pool.map(_draw_one, batch)):
+                if x is None:
+                    log(f"[learn] skip relation {j}: {y}")
+                elif done < count:
+                    done += 1
+                    yield spec, x, y
+            i += len(batch)
+
+
+def collect(ctx, specs, log, reps=2, keep=True):
+    """Features, labels (the best grid point) and per-relation rows for (spec, x, y) items.
+    With keep, a row also holds the relation (host columns) for a later evaluation."""
     import torch
     feats, labels, rows = [], [], []
     for k, (spec, x, y) in enumerate(specs):
         dx = torch.from_numpy(x).cuda()
         dy = torch.from_numpy(y).cuda()
         f = ctx.features(dx, dy)
-        times = sweep(ctx, dx, dy, x, y, log)
+        times = sweep(ctx, dx, dy, x, y, log, reps=reps)
         (b1, b2), tbest = min(times.items(), key=lambda kv: kv[1])
-        tcost, st = query_ms(ctx, dx, dy, "cost_model")
+        tcost, st = query_ms(ctx, dx, dy, "cost_model", reps=max(reps, 2))
         feats.append(f)
         labels.append([math.log(b1), math.log(b2)])
-        rows.append(dict(spec=spec, best=(b1, b2), t_best=tbest, t_cost=tcost,
-                         cost_delta=(st["delta1"], st["delta2"]), x=dx, y=dy))
-        torch.cuda.empty_cache()
-        log(f"[learn] {k + 1}/{len(specs)} N={spec['n']} best={b1},{b2} {tbest:.2f} ms "
-            f"cost-model {tcost:.2f} ms")
+        row = dict(spec=spec, best=(b1, b2), t_best=tbest, t_cost=tcost,
+                   cost_delta=(st["delta1"], st["delta2"]))
+        if keep:
+            row.update(hx=x, hy=y)
+        rows.append(row)
+        del dx, dy
+        if k % 25 == 0 or k < 5:
+            log(f"[learn] {k + 1} N={spec['n']} best={b1},{b2} {tbest:.2f} ms "
+                f"cost-model {tcost:.2f} ms")
     return np.array(feats, np.float32), np.array(labels, np.float32), rows
 
 
@@ -178,10 +206,13 @@ def fit(pred, X, T, steps: int, lr: float, seed: int, log):
 
 
 def evaluate(ctx, pred, rows, log):
+    import torch
     ctx.set_predictor(pred)
     out = []
     for r in rows:
-        t_learn, st = query_ms(ctx, r["x"], r["y"], "learned")
+        dx, dy = torch.from_numpy(r["hx"]).cuda(), torch.from_numpy(r["hy"]).cuda()
+        t_learn, st = query_ms(ctx, dx, dy, "learned")
+        del dx, dy
         out.append(dict(n=r["spec"]["n"], best=r["best"], t_best=r["t_best"], t_cost=r["t_cost"],
                         t_learned=t_learn, learned_delta=(st["delta1"], st["delta2"]),
                         cost_delta=r["cost_delta"], overruled=st["learned_judged"] == 2))
@@ -210,8 +241,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--max-join", type=float, default=1e9)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--reps", type=int, default=1, help="runs per grid point (the fastest is kept)")
     ap.add_argument("--out", default=None, help="write the trained float32 parameters (.npy)")
     ap.add_argument("--report", default=None, help="write a JSON report")
+    ap.add_argument("--data", default=None, help="write the features and labels (.npz)")
+    ap.add_argument("--budget-s", type=float, default=0.0,
+                    help="stop drawing training relations after this many seconds (0: no limit)")
     ap.add_argument("--eval", default=None, metavar="PARAMS",
                     help="no training: evaluate these parameters (.npy) on the held-out relations")
     args = ap.parse_args(argv)
@@ -223,24 +258,42 @@ def main(argv=None):
         print(*a, file=sys.stderr, flush=True)
 
     t0 = time.time()
-    # the relations are drawn by spawned workers before this process touches the GPU
-    specs = draw_specs(args.train + args.test, args.seed, args.n_lo, args.n_hi, args.max_join, log)
+    # the relations are drawn by spawned workers while the GPU sweeps earlier ones; the
+    # held-out relations are the ones after the training relations in the same draw
+    stream = stream_specs(args.train + args.test, args.seed, args.n_lo, args.n_hi,
+                          args.max_join, log)
     ctx = jp.Context(0)
     pred = jp.Predictor(0)
     if args.eval:
-        # the held-out relations are the same ones as when training (same draw)
-        X, T, rows = collect(ctx, specs[args.train:], log)
+        import itertools
+        X, T, rows = collect(ctx, itertools.islice(stream, args.test), log, reps=args.reps)
         pred.set_params(np.load(args.eval))
         summary, detail = evaluate(ctx, pred, rows, log)
         summary.update(train_relations=args.train, evaluated=os.path.basename(args.eval),
                        seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
     else:
-        X, T, rows = collect(ctx, specs, log)
-        Xtr, Ttr = X[:args.train], T[:args.train]
+        import itertools
+        # held-out relations first (the first args.test of the draw), then training
+        # relations until args.train or the time budget
+        Xte, Tte, rows = collect(ctx, itertools.islice(stream, args.test), log, reps=args.reps)
+        budget = args.budget_s
+
+        def until_budget(it):
+            for item in it:
+                if budget and time.time() - t0 > budget:
+                    log(f"[learn] time budget reached")
+                    return
+                yield item
+        Xtr, Ttr, _ = collect(ctx, until_budget(stream), log, reps=args.reps, keep=False)
+        log(f"[learn] {len(Xtr)} training and {len(Xte)} held-out relations swept in "
+            f"{time.time() - t0:.0f} s")
         loss = fit(pred, Xtr, Ttr, args.steps, args.lr, args.seed, log)
-        summary, detail = evaluate(ctx, pred, rows[args.train:], log)
-        summary.update(train_relations=args.train, final_train_loss=loss,
+        summary, detail = evaluate(ctx, pred, rows, log)
+        summary.update(train_relations=len(Xtr), final_train_loss=loss, reps_per_point=args.reps,
+                       n_range=[args.n_lo, args.n_hi], max_join=args.max_join,
                        seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
+        if args.data:
+            np.savez(args.data, Xtr=Xtr, Ttr=Ttr, Xte=Xte, Tte=Tte)
     if args.out:
         np.save(args.out, pred.get_params())
     if args.report:
