@@ -64,6 +64,28 @@ def candidate_counts(rx, ry):
     return ux, cand
 
 
+# ----------------------------------------------------------------- ranks
+def shard_plan(rx, ry, world, rank):
+    """Rank boundaries over x (contiguous ranges of near-equal light-candidate weight) and
+    rank `rank`'s tuples of R (paper_2002_12459_gb300.shard)."""
+    from paper_2002_12459_gb300 import shard as SH
+    bounds = SH.x_bounds(rx, ry, world)
+    return bounds, SH.shard(rx, ry, rank, bounds)
+
+
+def reduce_over_ranks(value, op, world):
+    """max or sum of a host number over the ranks (torch.distributed; the value itself when
+    there is one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -423,8 +445,28 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    for i in range(args.warmup):
+    # N > 1: rank r answers the x-range shard r of the one query (its tuples of R against
+    # all of S) at the thresholds Algorithm 3 picks for the whole relation, found once
+    # before the timed steps; every rank then makes the same partition (x and z degrees
+    # are whole in each shard, y degrees come from S), and the ranks' outputs concatenated
+    # in rank order are the query's sorted output
+    bounds = None
+    if world > 1:
+        bounds, (qx, qy) = shard_plan(rx, ry, world, rank)
+        dqx, dqy = torch.from_numpy(qx).cuda(), torch.from_numpy(qy).cuda()
         ox, oz = ctx.two_path(dx, dy)
+        plan = ctx.stats()
+        del ox, oz
+        ctx.set_threshold("fixed", plan["delta1"], plan["delta2"])
+
+        def query():
+            return ctx.two_path(dqx, dqy, dx, dy)
+    else:
+        def query():
+            return ctx.two_path(dx, dy)
+
+    for i in range(args.warmup):
+        ox, oz = query()
         del ox, oz
         torch.cuda.synchronize()
         log(f"[bench] warmup {i}: {ctx.stats()['ms_pass'][12]:.2f} ms")
@@ -439,7 +481,7 @@ def run_ours(args, rank, world, local_rank):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(ctx.stream)
-        ox, oz = ctx.two_path(dx, dy)
+        ox, oz = query()
         ev1.record(ctx.stream)
         torch.cuda.synchronize()
         barrier()
@@ -456,15 +498,13 @@ def run_ours(args, rank, world, local_rank):
     st = stats[-1]
     out = st["out_count"]
     mean_ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([mean_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = reduce_over_ranks(mean_ms, "max", world)
+    total_out = int(reduce_over_ranks(out, "sum", world))
 
     # end to end through the C-ABI with host buffers, right after the timed
     # steps (same workspace and allocator state as the steps it is compared with)
     e2e = None
-    if rank == 0 and not args.no_e2e:
+    if world == 1 and not args.no_e2e:
         # host input columns in, the result written by the output kernel straight into
         # pinned host columns (jp_two_path_into): every byte crosses the host link
         hrx = torch.from_numpy(rx).pin_memory()
@@ -501,7 +541,7 @@ def run_ours(args, rank, world, local_rank):
     # the same query at the learned thresholds (the shipped predictor), timed
     # the same way, against the cost-model thresholds above
     learned = None
-    if rank == 0 and not args.no_learned and args.mode == "cost_model":
+    if world == 1 and not args.no_learned and args.mode == "cost_model":
         learned = learned_vs_cost_model(ctx, dx, dy, flush, mean_ms, st, args)
 
     # sampled bit-exact check of the last result against the per-row oracle
@@ -515,7 +555,11 @@ def run_ours(args, rank, world, local_rank):
         ux = np.unique(rx)
         rng = np.random.default_rng(0)
         ux_c, cand = candidate_counts(rx, ry)
-        sample = list(rng.choice(ux, 24, replace=False)) + list(ux_c[np.argsort(-cand)[:4]])
+        if bounds is not None:           # rows of this rank's shard only
+            keep = (ux >= bounds[rank]) & (ux < bounds[rank + 1])
+            keep_c = (ux_c >= bounds[rank]) & (ux_c < bounds[rank + 1])
+            ux, ux_c, cand = ux[keep], ux_c[keep_c], cand[keep_c]
+        sample = list(rng.choice(ux, min(24, len(ux)), replace=False)) + list(ux_c[np.argsort(-cand)[:4]])
         ok = True
         for a in sample:
             s, e = np.searchsorted(hx, a, "left"), np.searchsorted(hx, a, "right")
@@ -526,7 +570,7 @@ def run_ours(args, rank, world, local_rank):
     del ox, oz
 
     base = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:
         base = cpu_baseline(rx, ry, args.cpu_cand, full=args.cpu_full)
 
     peaks, kind = load_peaks()
@@ -537,7 +581,7 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return None
     extra = None
-    if not args.no_extra:
+    if world == 1 and not args.no_extra:
         extra = {}
         for name, fn in (("two_path_uniform_20k", lambda: run_uniform(args)),
                          ("star3_2m", lambda: run_star(args, "star3_2m"))):
@@ -551,18 +595,20 @@ def run_ours(args, rank, world, local_rank):
                                                    "roofline", "kernel_rooflines", "cpu_baseline",
                                                    "parity", "gpu_launches")}
     return {
-        "metric": METRIC, "value": world * out / (max_ms * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": total_out / (max_ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
         "config": {"workload": args.workload, "n_tuples": wl["n"], "dom_x": wl["dom_x"],
                    "gamma_x": wl["gamma_x"], "dom_y": wl["dom_y"], "gamma_y": wl["gamma_y"],
                    "seed": wl["seed"], "query": "two-path self-join Q(x,z)=R(x,y),R(z,y)",
                    "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
-                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": out,
+                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": total_out,
                    "light_candidates": st["light_candidates"], "out_join": st["out_join"],
                    "heavy_gemm": "tcgen05 kind::f8f6f4, E4M3 0/1 operands, exact FP32 accumulate",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "parallelism": (f"x-range shards of one query on {world} ranks, no collective on "
+                                   "the data path" if world > 1 else "single GPU"),
                    "l2": "256 MiB flush written before every step",
                    "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
         "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
@@ -841,7 +887,7 @@ def run_ssj(args):
                    "order": "count descending, ties in (x, z) order",
                    "query": "SSJ: (a, c, |R[a] ∩ R[c]|) with |R[a] ∩ R[c]| >= c_min",
                    "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
-                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": out,
+                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": total_out,
                    "light_candidates": st["light_candidates"], "x_ranges": st["count_ranges"],
                    "light_pairs": st["count_light_pairs"], "heavy_pairs": st["heavy_pairs"],
                    "l2": "256 MiB flush written before every step",

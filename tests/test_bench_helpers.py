@@ -128,3 +128,43 @@ def test_clock_record_median_under_load_and_reasons(tmp_path):
     rec = cs.stop()
     assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0   # idle sample left out
     assert rec["reasons"] == ["sw_power_cap"] and rec["samples"] == 4
+
+
+def _sharded_rank(rank, world, port, out_path):
+    import os
+    import torch.distributed as dist
+    import oracle
+    from paper_2002_12459_gb300 import workloads as W
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(9)
+        rx, ry = W.random_small_relation(rng, 3000, 250, 90, -120, 5, 0.8)
+        bounds, (qx, qy) = bench.shard_plan(rx, ry, world, rank)
+        ox, oz = oracle.two_path(qx, qy, rx, ry)           # the rank's shard against all of S
+        total = bench.reduce_over_ranks(len(ox), "sum", world)
+        slowest = bench.reduce_over_ranks(float(rank + 1), "max", world)
+        parts = [None] * world
+        dist.all_gather_object(parts, (ox.tolist(), oz.tolist()))
+        if rank == 0:
+            wx, wz = oracle.two_path(rx, ry)
+            gx = np.concatenate([np.array(p[0], np.int32) for p in parts])
+            gz = np.concatenate([np.array(p[1], np.int32) for p in parts])
+            ok = (total == len(wx) and slowest == float(world) and np.array_equal(gx, wx)
+                  and np.array_equal(gz, wz))
+            with open(out_path, "w") as f:
+                f.write("ok" if ok else f"bad {total} {len(wx)} {slowest}")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_bench_logic_on_two_gloo_ranks(tmp_path, oracle_mod):
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = tmp_path / "result.txt"
+    mp.start_processes(_sharded_rank, args=(2, port, str(out)), nprocs=2, join=True,
+                       start_method="spawn")
+    assert out.read_text() == "ok"
