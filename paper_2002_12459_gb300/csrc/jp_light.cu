@@ -42,7 +42,8 @@ constexpr int W_CAP = 256;            // small warp class capacity
 constexpr int W2_CAP = 2048;          // warp bucket class capacity
 constexpr int M_CAP = 4096;           // merge class capacity (one block per x)
 constexpr int M2_CAP = 8192;          // larger merge class capacity
-constexpr int M_THREADS = 256;
+constexpr int M_THREADS = 256;       // threads per row of the merge classes above 2048 candidates
+constexpr int M0_THREADS = 128;      // threads per row of the merge class up to 2048 candidates
 constexpr int M_MAXL = 64;            // merge class: at most this many neighbour lists
 constexpr int BM_THREADS = 1024;
 constexpr int BM_MAX_WORDS = 52 * 1024;  // bitmap window: 208 KB + 6.5 KB summary + 12 KB counters/bounds
@@ -544,13 +545,13 @@ __device__ __forceinline__ int32_t co_rank(const int32_t* A, int32_t la, const i
     return lo;
 }
 
-template <int CAP>
-__global__ void __launch_bounds__(M_THREADS)
+template <int CAP, int TPB>
+__global__ void __launch_bounds__(TPB)
     light_merge_kernel(LightArgs A, const int32_t* queue, const Counters* qc, int qid) {
     extern __shared__ int32_t dyn_m[];
     __shared__ int32_t s_runs[2][M_MAXL + 1];   // run boundaries, current and next level
     __shared__ int32_t s_start[M_MAXL];         // list starts in szval
-    __shared__ uint32_t s_wsum[M_THREADS / 32];
+    __shared__ uint32_t s_wsum[TPB / 32];
     __shared__ unsigned long long s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t nq = qc->q[qid];
@@ -602,11 +603,11 @@ __global__ void __launch_bounds__(M_THREADS)
         // only grow, so its run index k only moves forward
         constexpr int U = 8;
         int k = 0;
-        for (int32_t f0 = tid; f0 < c; f0 += U * M_THREADS) {
+        for (int32_t f0 = tid; f0 < c; f0 += U * TPB) {
             int32_t zz[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int32_t f = f0 + u * M_THREADS;
+                const int32_t f = f0 + u * TPB;
                 zz[u] = 0;
                 if (f < c) {
                     while (s_runs[0][k + 1] <= f) ++k;
@@ -615,14 +616,14 @@ __global__ void __launch_bounds__(M_THREADS)
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int32_t f = f0 + u * M_THREADS;
+                const int32_t f = f0 + u * TPB;
                 if (f < c) src[f] = zz[u];
             }
         }
         __syncthreads();
         // pairwise merge levels
         int runs = deg, cur = 0;
-        const int32_t per = (c + M_THREADS - 1) / M_THREADS;
+        const int32_t per = (c + TPB - 1) / TPB;
         while (runs > 1) {
             const int32_t* rb = s_runs[cur];
             const int pairs = (runs + 1) >> 1;
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(M_THREADS)
         }
         // deduplicate neighbours: warp w owns a range of whole 32-value rounds
         const int32_t rounds = (c + 31) >> 5;
-        const int32_t rpw = (rounds + (M_THREADS / 32) - 1) / (M_THREADS / 32);
+        const int32_t rpw = (rounds + (TPB / 32) - 1) / (TPB / 32);
         const int32_t wb = min(c, warp * rpw * 32), we = min(c, wb + rpw * 32);
         uint32_t mine = 0;
         for (int32_t i = wb + lane; i - lane < we; i += 32) {
@@ -675,7 +676,7 @@ __global__ void __launch_bounds__(M_THREADS)
         __syncthreads();
         uint32_t before = 0, total = 0;
 #pragma unroll
-        for (int k = 0; k < M_THREADS / 32; ++k) {
+        for (int k = 0; k < TPB / 32; ++k) {
             const uint32_t v = s_wsum[k];
             before += k < warp ? v : 0u;
             total += v;
@@ -1089,21 +1090,21 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         const size_t sm0 = (size_t)2 * W2_CAP * sizeof(int32_t);   // 16 KB: 8 blocks per SM
         const size_t sm1 = (size_t)2 * M_CAP * sizeof(int32_t);
         const size_t sm2 = (size_t)2 * M2_CAP * sizeof(int32_t);
-        smem_limit((const void*)light_merge_kernel<M_CAP>, sm1);
-        smem_limit((const void*)light_merge_kernel<M2_CAP>, sm2);
+        smem_limit((const void*)light_merge_kernel<M_CAP, M_THREADS>, sm1);
+        smem_limit((const void*)light_merge_kernel<M2_CAP, M_THREADS>, sm2);
         tbegin(TM_LIGHT_MERGE);
         if (hc.q[Q_MERGE2]) {
-            light_merge_kernel<M2_CAP><<<grid_for(hc.q[Q_MERGE2], 1, 152 * 3), M_THREADS, sm2, st>>>(
+            light_merge_kernel<M2_CAP, M_THREADS><<<grid_for(hc.q[Q_MERGE2], 1, 152 * 3), M_THREADS, sm2, st>>>(
                 A, queues + (int64_t)Q_MERGE2 * nx, ctr, Q_MERGE2);
             JP_CHECK_LAUNCH();
         }
         if (hc.q[Q_MERGE]) {
-            light_merge_kernel<M_CAP><<<grid_for(hc.q[Q_MERGE], 1, 152 * 6), M_THREADS, sm1, st>>>(
+            light_merge_kernel<M_CAP, M_THREADS><<<grid_for(hc.q[Q_MERGE], 1, 152 * 6), M_THREADS, sm1, st>>>(
                 A, queues + (int64_t)Q_MERGE * nx, ctr, Q_MERGE);
             JP_CHECK_LAUNCH();
         }
         if (hc.q[Q_MERGE0]) {
-            light_merge_kernel<W2_CAP><<<grid_for(hc.q[Q_MERGE0], 1, 152 * 8), M_THREADS, sm0, st>>>(
+            light_merge_kernel<W2_CAP, M0_THREADS><<<grid_for(hc.q[Q_MERGE0], 1, 152 * 12), M0_THREADS, sm0, st>>>(
                 A, queues + (int64_t)Q_MERGE0 * nx, ctr, Q_MERGE0);
             JP_CHECK_LAUNCH();
         }
