@@ -114,8 +114,10 @@ typedef struct {
                                   candidate fill, 14 sort and run lengths, 15 heavy rows,
                                   merge and output, each summed over the x ranges */
     int64_t learned_judged;    /* JP_LEARNED only: 1 the model's thresholds were used, 2 the cost
-                                  model judged them too costly (modelled cost above 3 x that of
-                                  Algorithm 3's thresholds) and Algorithm 3's were used; else 0 */
+                                  model judged them too costly (modelled cost above judge x that
+                                  of Algorithm 3's thresholds, or a heavy block -- FP8 operands
+                                  and the product's bit matrix -- above half of the free device
+                                  memory) and Algorithm 3's were used; else 0 */
     int64_t filter_pairs;      /* jp_two_path_filter only: distinct candidate pairs of T */
     int64_t filter_query_out;  /* jp_two_path_filter only: |OUT| of the query on the reduced R and S
                                   (out_count is then the number of pairs of T answered) */
@@ -163,7 +165,8 @@ typedef struct {
     double eps;          /* descent step, 0 < eps < 1 */
     double wcoj_factor;  /* plain worst-case optimal join when OUT_join <= wcoj_factor N, >= 0 */
     double judge;        /* JP_LEARNED keeps the model's thresholds unless they cost more than
-                            judge times Algorithm 3's choice, >= 1 */
+                            judge times Algorithm 3's choice (or their heavy block does not
+                            fit in half of the free device memory), >= 1 */
 } jp_cost_model;
 
 /* Replace the context's constants (copied; NULL restores the defaults, which were measured on

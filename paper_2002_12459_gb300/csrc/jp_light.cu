@@ -146,13 +146,27 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // Thread per x: class, queue slot (warp-aggregated atomics), block-aggregated sums.
+// Scratch a row of x reserves: its distinct z can outnumber neither its
+// light candidates c plus (heavy x) the w columns of its product row, nor all
+// of its join candidates (xsum, summed over light and heavy y), nor |dom z|.
+__device__ __forceinline__ unsigned long long row_bound(unsigned long long c, bool heavy,
+                                                        int64_t w, int64_t nz,
+                                                        const int64_t* xsum, int64_t a) {
+    unsigned long long ub = c;
+    if (heavy) {
+        ub += (unsigned long long)w;
+        if (xsum && ub > (unsigned long long)xsum[a]) ub = (unsigned long long)xsum[a];
+    }
+    return ub > (unsigned long long)nz ? (unsigned long long)nz : ub;
+}
+
 // A light x with a single neighbour list needs no deduplication: S[b] is
 // sorted and distinct, so the output pass reads it in place (tmp_off holds
 // -(offset in szval) - 1) and no scratch is used.
 __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
                              const int32_t* rxoff, const int32_t* rycol, const int32_t* syoff,
-                             int64_t w, int64_t nz, int32_t* queues, int32_t* cnt,
-                             int64_t* tmp_off, Counters* ctr) {
+                             const int64_t* xsum, int64_t w, int64_t nz, int32_t* queues,
+                             int32_t* cnt, int64_t* tmp_off, Counters* ctr) {
     __shared__ unsigned long long s_sum[2 + 2 * NQ];
     const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 2 + 2 * NQ; i += blockDim.x) s_sum[i] = 0;
@@ -174,8 +188,7 @@ __global__ void queue_kernel(int64_t nx, const int64_t* cand, const int32_t* hx,
                 ub = c;
             } else if (heavy || (c > (unsigned long long)W2_CAP && dg > 1)) {
                 q = (dg >= BM_WARP_PER_LIST || c >= (unsigned long long)HUB_CAND) ? Q_HUB : Q_BITMAP;
-                ub = c + (heavy ? (unsigned long long)w : 0ull);
-                if (ub > (unsigned long long)nz) ub = (unsigned long long)nz;
+                ub = row_bound(c, heavy, w, nz, xsum, a);
             } else if (c > 0 && rxoff[a + 1] - rxoff[a] == 1) {
                 q = Q_COPY;
                 cnt[a] = (int32_t)c;
@@ -294,6 +307,7 @@ struct LightArgs {
     int64_t w;
     int64_t nz;
     const int64_t* cand;
+    const int64_t* xsum;   // [nx] each x's join candidates over all its y (may be null)
     int32_t* tmp;
     int64_t tmp_cap;
     int64_t* tmp_off;
@@ -808,9 +822,8 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
         const bool heavy = h >= 0;
         const int2* yb = heavy ? A.ybh : A.ybl;
         const int32_t e0 = A.rxoff[a], deg = A.rxoff[a + 1] - e0;
-        unsigned long long ub = (unsigned long long)A.cand[a] +
-                                (heavy ? (unsigned long long)A.w : 0ull);
-        if (ub > (unsigned long long)A.nz) ub = (unsigned long long)A.nz;
+        const unsigned long long ub =
+            row_bound((unsigned long long)A.cand[a], heavy, A.w, A.nz, A.xsum, a);
         // read only after the marking phase's barriers: its latency overlaps them
         if (threadIdx.x == 0) s_base = atomicAdd(&A.ctr->cursor, ub);
         unsigned long long running = 0;
@@ -1015,7 +1028,8 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
         nx, g.rxoff, g.rycol, p.hx, ybh, g.deg_sy, g.xsum, cand);
     JP_CHECK_LAUNCH();
     queue_kernel<<<grid_for(nx, 256, 152 * 8), 256, 0, st>>>(
-        nx, cand, p.hx, g.rxoff, g.rycol, g.syoff, p.w, g.nz, queues, lr.cnt, lr.tmp_off, ctr);
+        nx, cand, p.hx, g.rxoff, g.rycol, g.syoff, g.xsum, p.w, g.nz, queues, lr.cnt, lr.tmp_off,
+        ctr);
     JP_CHECK_LAUNCH();
     tend(TM_CLASSIFY);
     Counters hc;
@@ -1057,6 +1071,7 @@ void light_and_union(const Graph& g, const Partition& p, const Heavy& h, LightRe
     A.w = p.w;
     A.nz = g.nz;
     A.cand = cand;
+    A.xsum = g.xsum;
     A.tmp = lr.tmp;
     A.tmp_cap = lr.tmp_cap;
     A.tmp_off = lr.tmp_off;

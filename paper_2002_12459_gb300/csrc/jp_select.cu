@@ -313,7 +313,15 @@ void select_thresholds(const Graph& g, int mode, int64_t fd1, int64_t fd2, int64
     }
     if (mode == JP_LEARNED) {
         const double cl = cost((double)l1, (double)l2), ca = cost(pa, pb);
-        if (cl <= K.judge * ca) {
+        // the prediction's heavy block: FP8 operands (u x v, w x v bytes) and
+        // the product's bit matrix (u x w bits); it must also fit in half of
+        // the device memory that is free now
+        const double u = IX.gt_count((double)l2), v = IY.gt_count((double)l1),
+                     w = IZ.gt_count((double)l2);
+        size_t free_b = 0, total_b = 0;
+        JP_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        const bool fits = v * (u + w) + u * w / 8.0 <= 0.5 * (double)free_b;
+        if (fits && cl <= K.judge * ca) {
             *d1 = l1;
             *d2 = l2;
             if (judged) *judged = 1;

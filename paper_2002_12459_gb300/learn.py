@@ -10,7 +10,8 @@ and evaluated on held-out relations: the query time at the predicted
 thresholds is compared with the best grid time ("oracle-best threshold") and
 with the time at the cost-model thresholds (Algorithm 3), which is also the
 fallback when no model is set and the judge of every prediction (a
-prediction whose modelled cost exceeds 3x that of Algorithm 3's choice is
+prediction whose modelled cost exceeds 3x that of Algorithm 3's choice, or
+whose heavy block would not fit in half of the free device memory, is
 replaced by that choice).
 
   python -m paper_2002_12459_gb300.learn --train 200 --test 48 --n-hi 5e6 --max-join 2e9 \
@@ -67,11 +68,10 @@ def heavy_bound(x, y, d1, d2):
 
 
 # grid points whose heavy block is beyond these bounds are not run (their time
-# is taken as infinite): operands over 16 GB, a product over ~2 s, or light
-# scratch over 64 GB (every heavy x reserves room for its product row: u * u)
+# is taken as infinite): FP8 operands and the product's bit matrix over 16 GB,
+# or a product over ~2 s
 MAX_BLOCK_BYTES = 16e9
 MAX_BLOCK_OPS = 4e15
-MAX_SCRATCH_BYTES = 64e9
 
 
 def sweep(ctx, dx, dy, x, y, log=None, reps=2):
@@ -81,8 +81,7 @@ def sweep(ctx, dx, dy, x, y, log=None, reps=2):
     for d1 in D1_GRID:
         for d2 in D2_GRID:
             u, v = heavy_bound(x, y, d1, d2)
-            if (2.0 * u * v > MAX_BLOCK_BYTES or 2.0 * u * v * u > MAX_BLOCK_OPS
-                    or 4.0 * u * u > MAX_SCRATCH_BYTES):
+            if 2.0 * u * v + u * u / 8.0 > MAX_BLOCK_BYTES or 2.0 * u * v * u > MAX_BLOCK_OPS:
                 times[(d1, d2)] = math.inf
                 continue
             try:
@@ -172,8 +171,9 @@ def collect(ctx, specs, log, reps=2, keep=True):
         tcost, st = query_ms(ctx, dx, dy, "cost_model", reps=max(reps, 2))
         feats.append(f)
         labels.append([math.log(b1), math.log(b2)])
+        grid = [[times[(d1, d2)] for d2 in D2_GRID] for d1 in D1_GRID]
         row = dict(spec=spec, best=(b1, b2), t_best=tbest, t_cost=tcost,
-                   cost_delta=(st["delta1"], st["delta2"]))
+                   cost_delta=(st["delta1"], st["delta2"]), grid=grid)
         if keep:
             row.update(hx=x, hy=y)
         rows.append(row)
@@ -182,6 +182,64 @@ def collect(ctx, specs, log, reps=2, keep=True):
             log(f"[learn] {k + 1} N={spec['n']} best={b1},{b2} {tbest:.2f} ms "
                 f"cost-model {tcost:.2f} ms")
     return np.array(feats, np.float32), np.array(labels, np.float32), rows
+
+
+def _remake(spec):
+    x, y = make_relation(spec)
+    return spec, x, y
+
+
+def remake_rows(rows, workers=None):
+    """Regenerate the relations of saved held-out rows (their seeded specs), by spawned
+    workers; call before the first GPU call of the process."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+        for r, (_, x, y) in zip(rows, pool.map(_remake, [r["spec"] for r in rows])):
+            r.update(hx=x, hy=y)
+    return rows
+
+
+def compare(ctx, rows, arms, log):
+    """Query time of each arm on each saved held-out relation (rows hold the relation and
+    the grid's best time).  arms: name -> (threshold mode, cost-model constants or None,
+    predictor or None).  A failed query is recorded and counted at infinity."""
+    import torch
+    from paper_2002_12459_gb300 import jp
+    out = []
+    for r in rows:
+        dx, dy = torch.from_numpy(r["hx"]).cuda(), torch.from_numpy(r["hy"]).cuda()
+        rec = dict(n=r["spec"]["n"], t_best=r["t_best"], best=r["best"])
+        for name, (mode, consts, pred) in arms.items():
+            if consts:
+                ctx.set_cost_model(**consts)
+            else:
+                ctx.set_cost_model()
+            ctx.set_predictor(pred)
+            try:
+                t, st = query_ms(ctx, dx, dy, mode)
+                rec[name] = dict(t=t, delta=(st["delta1"], st["delta2"]),
+                                 judged=st["learned_judged"])
+            except jp.JPError as e:
+                torch.cuda.empty_cache()
+                rec[name] = dict(t=math.inf, error=str(e))
+                log(f"[learn] N={r['spec']['n']} {name}: {e}")
+        ctx.set_predictor(None)
+        ctx.set_cost_model()
+        del dx, dy
+        out.append(rec)
+    summary = dict(relations=len(out))
+    for name in arms:
+        ratio = np.array([o[name]["t"] / o["t_best"] for o in out])
+        summary[name] = dict(over_best_geomean=float(np.exp(np.mean(np.log(ratio)))),
+                             within_10pct=int((ratio <= 1.1).sum()),
+                             total_ms=float(sum(o[name]["t"] for o in out)),
+                             failed=int((~np.isfinite(ratio)).sum()))
+    summary["best_total_ms"] = float(sum(o["t_best"] for o in out))
+    log("[learn] " + ", ".join(f"{k} {v['over_best_geomean']:.3f}" for k, v in summary.items()
+                               if isinstance(v, dict)))
+    return summary, out
 
 
 def init_params(seed: int = 0) -> np.ndarray:
@@ -195,27 +253,45 @@ def init_params(seed: int = 0) -> np.ndarray:
     return np.concatenate(parts).astype(np.float32)
 
 
-def fit(pred, X, T, steps: int, lr: float, seed: int, log):
+def fit(pred, X, T, steps: int, lr: float, seed: int, log, batch: int = 1024):
+    """Adam on the library's kernels; each step a seeded random mini-batch of at most
+    `batch` relations (the kernels take up to JP_MLP_MAX_BATCH rows)."""
     pred.set_params(init_params(seed))
+    rng = np.random.default_rng(seed + 1)
     loss = None
     for s in range(steps):
-        loss = pred.train_step(X, T, lr)
+        if len(X) > batch:
+            pick = rng.choice(len(X), batch, replace=False)
+            loss = pred.train_step(X[pick], T[pick], lr)
+        else:
+            loss = pred.train_step(X, T, lr)
         if s % 500 == 0 or s == steps - 1:
             log(f"[learn] step {s}: loss {loss:.4f}")
     return loss
 
 
 def evaluate(ctx, pred, rows, log):
+    """Query time at the learned thresholds on each held-out relation.  A query that
+    fails (out of device memory) is recorded with its error and counted at the
+    cost-model time, so that one failure neither ends the run nor flatters the model."""
     import torch
+    from paper_2002_12459_gb300 import jp
     ctx.set_predictor(pred)
     out = []
     for r in rows:
         dx, dy = torch.from_numpy(r["hx"]).cuda(), torch.from_numpy(r["hy"]).cuda()
-        t_learn, st = query_ms(ctx, dx, dy, "learned")
+        err = None
+        try:
+            t_learn, st = query_ms(ctx, dx, dy, "learned")
+            ld, judged = (st["delta1"], st["delta2"]), st["learned_judged"]
+        except jp.JPError as e:
+            torch.cuda.empty_cache()
+            err, t_learn, ld, judged = str(e), r["t_cost"], None, 0
+            log(f"[learn] held-out N={r['spec']['n']}: {e}")
         del dx, dy
         out.append(dict(n=r["spec"]["n"], best=r["best"], t_best=r["t_best"], t_cost=r["t_cost"],
-                        t_learned=t_learn, learned_delta=(st["delta1"], st["delta2"]),
-                        cost_delta=r["cost_delta"], overruled=st["learned_judged"] == 2))
+                        t_learned=t_learn, learned_delta=ld, cost_delta=r["cost_delta"],
+                        overruled=judged == 2, error=err))
     ctx.set_predictor(None)
     ratio_l = [o["t_learned"] / o["t_best"] for o in out]
     ratio_c = [o["t_cost"] / o["t_best"] for o in out]
@@ -225,7 +301,8 @@ def evaluate(ctx, pred, rows, log):
                    learned_total_ms=float(sum(o["t_learned"] for o in out)),
                    cost_total_ms=float(sum(o["t_cost"] for o in out)),
                    best_total_ms=float(sum(o["t_best"] for o in out)),
-                   overruled_by_cost_model=int(sum(o["overruled"] for o in out)))
+                   overruled_by_cost_model=int(sum(o["overruled"] for o in out)),
+                   failed=int(sum(o["error"] is not None for o in out)))
     log(f"[learn] held-out: learned/best {summary['learned_over_best_geomean']:.3f}, "
         f"cost-model/best {summary['cost_over_best_geomean']:.3f}")
     return summary, out
@@ -249,6 +326,12 @@ def main(argv=None):
                     help="stop drawing training relations after this many seconds (0: no limit)")
     ap.add_argument("--eval", default=None, metavar="PARAMS",
                     help="no training: evaluate these parameters (.npy) on the held-out relations")
+    ap.add_argument("--compare", default=None, metavar="DATA",
+                    help="no sweep: time the held-out relations of a --data file at Algorithm "
+                         "3's default constants, at --cost-json's and at --params' predictions")
+    ap.add_argument("--params", default=None, help="predictor parameters (.npy) for --compare")
+    ap.add_argument("--cost-json", default=None,
+                    help="fitted cost-model constants (calibrate.py output) for --compare")
     args = ap.parse_args(argv)
 
     from paper_2002_12459_gb300 import build, jp
@@ -256,6 +339,29 @@ def main(argv=None):
 
     def log(*a):
         print(*a, file=sys.stderr, flush=True)
+
+    if args.compare:
+        d = np.load(args.compare, allow_pickle=False)
+        rows = remake_rows([json.loads(str(v)) for v in d["held"]][:args.test])
+        ctx = jp.Context(0)
+        arms = {"cost_default": ("cost_model", None, None)}
+        if args.cost_json:
+            with open(args.cost_json) as f:
+                arms["cost_fitted"] = ("cost_model", json.load(f)["constants"], None)
+        pred = None
+        if args.params:
+            pred = jp.Predictor(0)
+            pred.set_params(np.load(args.params))
+            arms["learned"] = ("learned", None, pred)
+        summary, detail = compare(ctx, rows, arms, log)
+        if args.report:
+            with open(args.report, "w") as f:
+                json.dump(dict(summary=summary, held_out=detail), f, indent=1, default=str)
+        print(json.dumps(summary))
+        if pred:
+            pred.close()
+        ctx.close()
+        return
 
     t0 = time.time()
     # the relations are drawn by spawned workers while the GPU sweeps earlier ones; the
@@ -284,16 +390,20 @@ def main(argv=None):
                     log(f"[learn] time budget reached")
                     return
                 yield item
-        Xtr, Ttr, _ = collect(ctx, until_budget(stream), log, reps=args.reps, keep=False)
+        Xtr, Ttr, trows = collect(ctx, until_budget(stream), log, reps=args.reps, keep=False)
         log(f"[learn] {len(Xtr)} training and {len(Xte)} held-out relations swept in "
             f"{time.time() - t0:.0f} s")
+        if args.data:            # kept before fitting: the sweeps are the expensive part
+            def meta(rs):
+                return np.array([json.dumps({k: v for k, v in r.items() if k not in ("hx", "hy")},
+                                            default=str) for r in rs])
+            np.savez(args.data, Xtr=Xtr, Ttr=Ttr, Xte=Xte, Tte=Tte, held=meta(rows),
+                     train=meta(trows), d1_grid=np.array(D1_GRID), d2_grid=np.array(D2_GRID))
         loss = fit(pred, Xtr, Ttr, args.steps, args.lr, args.seed, log)
         summary, detail = evaluate(ctx, pred, rows, log)
         summary.update(train_relations=len(Xtr), final_train_loss=loss, reps_per_point=args.reps,
                        n_range=[args.n_lo, args.n_hi], max_join=args.max_join,
                        seconds=time.time() - t0, grid=[list(D1_GRID), list(D2_GRID)])
-        if args.data:
-            np.savez(args.data, Xtr=Xtr, Ttr=Ttr, Xte=Xte, Tte=Tte)
     if args.out:
         np.save(args.out, pred.get_params())
     if args.report:
