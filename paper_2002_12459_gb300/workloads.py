@@ -254,9 +254,17 @@ WORKLOADS = {
     "ssj_powerlaw_10m": dict(kind="ssj", gen="powerlaw", n=10_000_000,
                              dom_x=2_000_000, gamma_x=2.1,
                              dom_y=1_000_000, gamma_y=1.8, seed=0, c_min=2),
+    # the set similarity join on the 1M relation (profiling captures)
+    "ssj_powerlaw_1m": dict(kind="ssj", gen="powerlaw", n=1_000_000,
+                            dom_x=200_000, gamma_x=2.1,
+                            dom_y=100_000, gamma_y=1.8, seed=0, c_min=2),
     # star k = 3, 3 x 2M tuples, shared y domain 200k gamma 1.5, x uniform 500k
     "star3_2m": dict(kind="star", gen="star", k=3, n=2_000_000, dom_x=500_000,
                      dom_y=200_000, gamma_y=1.5, seed=0),
+    # a smaller star query for profiling captures: 3 x 1M tuples, y domain 250k (mean y
+    # degree 4 instead of 10, so that the output, ~1.7e8 triples, stays a few GB)
+    "star3_1m": dict(kind="star", gen="star", k=3, n=1_000_000, dom_x=250_000,
+                     dom_y=250_000, gamma_y=1.5, seed=0),
 }
 
 
