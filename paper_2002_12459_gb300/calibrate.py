@@ -13,7 +13,10 @@ power-law relations (the same self-join query): the model is linear in
 (T_I, T_s, 1/mm_rate, mm_fixed, T_m), so the fit is a non-negative least
 squares with a free intercept per relation (costs that do not depend on the
 thresholds: index build, output placement), each relation's times divided by
-its fastest, so that large and small relations weigh the same.
+its fastest, so that large and small relations weigh the same.  Only grid
+points within `cap` (default 3) times the relation's fastest enter the fit:
+thresholds are chosen near the optimum, and far-off points (a product of
+seconds, a light path ten times too slow) would otherwise set the constants.
 
   python -m paper_2002_12459_gb300.calibrate --data learn_data.npz --out cost_model.json
 
@@ -67,26 +70,39 @@ def features(degx, degy, cand, d1: float, d2: float):
             (u * v + u * w) if on else 0.0]
 
 
-def design(rows, log=None):
-    """(F, t, group) over every finite grid point of every relation: features, time
-    divided by the relation's fastest, and the relation's index.  A row holds the
-    relation's spec, its time grid (ms) and the grid's thresholds."""
+def relation_rows(r, cap: float = math.inf):
+    """Feature rows and relative times of one relation's grid points within cap times
+    its fastest."""
     from paper_2002_12459_gb300 import learn
-    F, t, grp = [], [], []
-    for k, r in enumerate(rows):
-        x, y = learn.make_relation(r["spec"])
-        degx, degy, cand, _ = degree_terms(x, y)
-        grid = np.asarray(r["grid"], np.float64)
-        best = np.min(grid)
-        for i, d1 in enumerate(r["d1_grid"]):
-            for j, d2 in enumerate(r["d2_grid"]):
-                if not math.isfinite(grid[i, j]):
-                    continue
+    x, y = learn.make_relation(r["spec"])
+    degx, degy, cand, _ = degree_terms(x, y)
+    grid = np.asarray(r["grid"], np.float64)
+    best = np.min(grid)
+    F, t = [], []
+    for i, d1 in enumerate(r["d1_grid"]):
+        for j, d2 in enumerate(r["d2_grid"]):
+            if math.isfinite(grid[i, j]) and grid[i, j] <= cap * best:
                 F.append(np.array(features(degx, degy, cand, d1, d2)) / (best * 1e-3))
                 t.append(grid[i, j] / best)
-                grp.append(k)
-        if log and k % 50 == 0:
-            log(f"[calibrate] {k + 1}/{len(rows)} relations")
+    return F, t
+
+
+def design(rows, log=None, workers=None, cap: float = math.inf):
+    """(F, t, group) over every finite grid point of every relation: features, time
+    divided by the relation's fastest, and the relation's index.  A row holds the
+    relation's spec, its time grid (ms) and the grid's thresholds.  The relations are
+    regenerated by a pool of spawned processes."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    F, t, grp = [], [], []
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+        for k, (f, tt) in enumerate(pool.map(relation_rows, rows, [cap] * len(rows))):
+            F += f
+            t += tt
+            grp += [k] * len(tt)
+            if log and k % 100 == 0:
+                log(f"[calibrate] {k + 1}/{len(rows)} relations")
     return np.array(F), np.array(t), np.array(grp)
 
 
@@ -136,6 +152,8 @@ def main(argv=None):
     ap.add_argument("--data", required=True, help="learn.py --data output (.npz)")
     ap.add_argument("--out", default=DEFAULT_OUT)
     ap.add_argument("--limit", type=int, default=0, help="use the first N relations only")
+    ap.add_argument("--cap", type=float, default=3.0,
+                    help="fit grid points within this factor of each relation's fastest")
     args = ap.parse_args(argv)
 
     def log(*a):
@@ -144,10 +162,10 @@ def main(argv=None):
     rows = load_rows(args.data)
     if args.limit:
         rows = rows[:args.limit]
-    F, t, grp = design(rows, log)
+    F, t, grp = design(rows, log, cap=args.cap)
     k, rms, rms0 = fit(F, t, grp)
     consts = constants(k, DEFAULT_BASE)
-    res = dict(constants=consts, fit=dict(relations=len(rows), points=int(len(t)),
+    res = dict(constants=consts, fit=dict(relations=len(rows), points=int(len(t)), cap=args.cap,
                                           rms_relative=rms, rms_relative_unfitted=rms0,
                                           vector=dict(zip(FIT_NAMES, map(float, k)))))
     with open(args.out, "w") as f:

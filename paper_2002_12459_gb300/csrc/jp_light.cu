@@ -637,7 +637,9 @@ __global__ void __launch_bounds__(TPB)
         __syncthreads();
         // pairwise merge levels
         int runs = deg, cur = 0;
-        const int32_t per = (c + TPB - 1) / TPB;
+        // a thread's share of the outputs; odd, so that the 32 lanes' stores
+        // (per words apart) fall in 32 different shared-memory banks
+        const int32_t per = ((c + TPB - 1) / TPB) | 1;
         while (runs > 1) {
             const int32_t* rb = s_runs[cur];
             const int pairs = (runs + 1) >> 1;
@@ -719,11 +721,21 @@ __global__ void __launch_bounds__(TPB)
 // Set bit r; a bit that was clear is a new distinct value of the row, counted
 // for the thread that owns its word in the emission (owner_shift: log2 of the
 // words a thread owns).
+// Word wi of the bitmap is stored at wi ^ (its owner's thread index mod 32):
+// in the emission walk all lanes of a warp visit the j-th word of their own
+// 32-word groups at the same time, and this spreads them over the 32 banks
+// (without it every lane reads bank j).  A warp reading a whole 32-word
+// group reads a permutation of it, also conflict-free.
+constexpr bool BM_SWZ = true;
+__device__ __forceinline__ int32_t bm_at(int32_t wi, int owner_shift) {
+    return BM_SWZ ? (wi ^ ((wi >> owner_shift) & 31)) : wi;
+}
+
 __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t* own, int owner_shift,
                                      int32_t r) {
     const int32_t wi = r >> 5;
     const uint32_t bit = 1u << (r & 31);
-    const uint32_t old = atomicOr(&bm[wi], bit);
+    const uint32_t old = atomicOr(&bm[bm_at(wi, owner_shift)], bit);
     if (old == 0) atomicOr(&summ[wi >> 5], 1u << (wi & 31));
     if (!(old & bit)) atomicAdd(&own[wi >> owner_shift], 1u);
 }
@@ -934,8 +946,9 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                         const int j = __ffs(m) - 1;
                         m &= m - 1;
                         const int32_t wi = s * 32 + j;
-                        uint32_t bits = bm[wi];
-                        bm[wi] = 0;
+                        const int32_t pw = bm_at(wi, owner_shift);
+                        uint32_t bits = bm[pw];
+                        bm[pw] = 0;
                         while (bits) {
                             const int bt = __ffs(bits) - 1;
                             bits &= bits - 1;
@@ -953,8 +966,9 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 for (int32_t g = g0; g < g1; ++g) {
                     if (summ[g] == 0) continue;
                     const int32_t wi = g * 32 + lane;
-                    const uint32_t wd = bm[wi];
-                    bm[wi] = 0;
+                    const int32_t pw = bm_at(wi, owner_shift);
+                    const uint32_t wd = bm[pw];
+                    bm[pw] = 0;
                     const uint32_t c = __popc(wd);
                     uint32_t inc = c;
 #pragma unroll

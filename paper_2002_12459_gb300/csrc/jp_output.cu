@@ -24,10 +24,6 @@ __global__ void widen_kernel(const int32_t* in, int64_t n, int64_t* out) {
 }
 
 constexpr int OUT_SX = 512;   // x entries staged in shared memory per tile
-constexpr int OUT_TILE = OUT_THREADS * OUT_VT;
-// staged tiles find each output's row by a block-wide scan instead of a
-// binary search per output
-constexpr bool OUT_LBS = true;
 
 // largest x in [lo, hi) with off[x] <= o (off non-decreasing, off[lo] <= o)
 __device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_t hi, int64_t o) {
@@ -62,45 +58,18 @@ __global__ void tile_start_kernel(const int64_t* __restrict__ out_off, int64_t n
     }
 }
 
-// Row of every output of a staged tile: each non-empty row writes its index
-// at its first output's position in s_row (zero elsewhere; row 0 holds the
-// tile's first output), and an inclusive max-scan over the tile carries each
-// index forward to the row's other outputs.  Thread t scans entries
-// [8t, 8t + 8).
-__device__ __forceinline__ void tile_rows(int32_t* s_row, int32_t* s_wmax) {
-    static_assert(OUT_VT == 8, "one pair of int4 per thread");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int4* q = reinterpret_cast<int4*>(s_row) + 2 * threadIdx.x;
-    const int4 a = q[0], b = q[1];
-    int32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int j = 1; j < 8; ++j) v[j] = max(v[j], v[j - 1]);
-    int32_t inc = v[7];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc = max(inc, y);
-    }
-    int32_t carry = __shfl_up_sync(0xffffffffu, inc, 1);
-    if (lane == 0) carry = 0;
-    if (lane == 31) s_wmax[warp] = inc;
-    __syncthreads();
-    for (int w = 0; w < warp; ++w) carry = max(carry, s_wmax[w]);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = max(v[j], carry);
-    q[0] = make_int4(v[0], v[1], v[2], v[3]);
-    q[1] = make_int4(v[4], v[5], v[6], v[7]);
-    __syncthreads();
-}
-
 // One tile of OUT_THREADS * OUT_VT consecutive outputs per block; when the
 // tile's x range is short its offsets are staged in shared memory.  Thread t
 // writes outputs o0 + t + k*OUT_THREADS, so each store instruction of a warp
 // covers 32 consecutive outputs.
 // X2: a second row column (the star's x2) is written next to the first.
 // VMAP: x and z values are ids into vmap, which gives the written values.
+// Bound by latency: a thread's loads are the only work in flight, so the
+// launch bound asks for 8 resident blocks per SM (2,048 threads, at most 32
+// registers each); measured faster than 5 or 6 blocks per SM.  The two-column
+// form (X2) holds more per output and is given 6.
 template <bool X2, bool VMAP>
-__global__ void __launch_bounds__(OUT_THREADS)
+__global__ void __launch_bounds__(OUT_THREADS, X2 ? 6 : 8)
     place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int32_t* __restrict__ tile_x,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
@@ -113,8 +82,6 @@ __global__ void __launch_bounds__(OUT_THREADS)
     __shared__ int64_t s_toff[OUT_SX];
     __shared__ int32_t s_xv[OUT_SX];
     __shared__ int32_t s_xv2[OUT_SX];
-    __shared__ __align__(16) int32_t s_row[OUT_TILE];
-    __shared__ int32_t s_wmax[OUT_THREADS / 32];
     const int64_t o0 = (int64_t)blockIdx.x * OUT_THREADS * OUT_VT;
     const int64_t o_last = min(count, o0 + (int64_t)OUT_THREADS * OUT_VT) - 1;
     // x range of the tile: from the x holding its first output to the x holding
@@ -131,18 +98,8 @@ __global__ void __launch_bounds__(OUT_THREADS)
             if (X2) s_xv2[i] = xval2[xlo + i];
         }
         if (threadIdx.x == 0) s_off[nxs] = (xhi < nx) ? out_off[xhi] : count;
-        if (OUT_LBS)
-            for (int j = threadIdx.x; j < OUT_TILE; j += OUT_THREADS) s_row[j] = 0;
     }
     __syncthreads();
-    if (OUT_LBS && staged) {
-        for (int64_t i = 1 + threadIdx.x; i < nxs; i += OUT_THREADS) {
-            const int64_t b = s_off[i] - o0;
-            if (b > 0 && b < OUT_TILE && s_off[i + 1] > s_off[i]) s_row[b] = (int32_t)i;
-        }
-        __syncthreads();
-        tile_rows(s_row, s_wmax);
-    }
     // all of a thread's list reads, then all of its id -> value gathers, then
     // the stores: OUT_VT independent loads in flight per phase
     int32_t zv[OUT_VT], xv[OUT_VT], xv2[OUT_VT];
@@ -156,8 +113,7 @@ __global__ void __launch_bounds__(OUT_THREADS)
         bool is_id = false;
         if (o <= o_last) {
             if (staged) {
-                const int64_t i = OUT_LBS ? (int64_t)s_row[threadIdx.x + k * OUT_THREADS]
-                                          : find_x(s_off, 0, nxs, o);
+                const int64_t i = find_x(s_off, 0, nxs, o);
                 zv[k] = list_at(tmp, szval, s_toff[i], o - s_off[i], &is_id);
                 xv[k] = s_xv[i];
                 if (X2) xv2[k] = s_xv2[i];
