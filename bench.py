@@ -379,6 +379,45 @@ def roofline(st, peaks, peak_kind, ms_by_slot, workload=None):
 
 
 # ----------------------------------------------------------------- learned thresholds
+# thresholds Algorithm 3 picks on the 10M relation with the constants measured on that
+# relation alone (the fitted defaults switch the heavy product off there)
+PRODUCT_DELTAS = (271, 35)
+
+
+def product_record(ctx, dx, dy, flush, args, peaks, kind):
+    """The same query at fixed thresholds with a heavy product (PRODUCT_DELTAS): its time and
+    the tensor-core product kernel's roofline, timed like the headline steps."""
+    import torch
+    ctx.set_threshold("fixed", *PRODUCT_DELTAS)
+    ms, gm, st = [], [], None
+    try:
+        for i in range(1 + max(args.steps, 3)):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(ctx.stream)
+            ox, oz = ctx.two_path(dx, dy)
+            ev1.record(ctx.stream)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            if i > 0:
+                ms.append(ev0.elapsed_time(ev1))
+                gm.append(st["ms_pass"][4])
+            del ox, oz
+    finally:
+        ctx.set_threshold(args.mode, args.delta1, args.delta2)
+    mean_ms, gemm_ms = sum(ms) / len(ms), sum(gm) / len(gm)
+    log(f"[bench] fixed thresholds {PRODUCT_DELTAS}: {mean_ms:.2f} ms, product {gemm_ms:.3f} ms")
+    return {"thresholds": list(PRODUCT_DELTAS), "ms_per_step": mean_ms, "steps": len(ms),
+            "u": st["u"], "v": st["v"], "w": st["w"], "out_count": st["out_count"],
+            "pass_ms": {k: round(v, 3) for k, v in enumerate(st["ms_pass"]) if v > 0},
+            "heavy_gemm": kernel_roofline(4, st, peaks, kind, gemm_ms),
+            "note": "Algorithm 3's choice with the constants measured on this relation alone; "
+                    "the headline uses the defaults fitted on 789 relations, which choose no "
+                    "heavy y here"}
+
+
 def learned_vs_cost_model(ctx, dx, dy, flush, cost_ms, st_cost, args):
     """Query time at the shipped predictor's thresholds (JP_LEARNED) next to
     the cost-model time just measured, plus the held-out summary written when
@@ -577,6 +616,10 @@ def run_ours(args, rank, world, local_rank):
     peaks.update(tensor_peaks)
     rl, rl_all = roofline(st, peaks, kind, slot_ms, args.workload)
     launches = sum(s["kernel_launches"] for s in stats)
+    product = None
+    if (world == 1 and not args.no_extra and args.workload == "two_path_powerlaw_10m"
+            and args.mode == "cost_model"):
+        product = product_record(ctx, dx, dy, flush, args, peaks, kind)
     ctx.close()
     if rank != 0:
         return None
@@ -613,6 +656,7 @@ def run_ours(args, rank, world, local_rank):
                    "pass_ms": {k: round(v, 3) for k, v in slot_ms.items() if v > 0}},
         "roofline": rl, "kernel_rooflines": rl_all, "cpu_baseline": base, "e2e": e2e, "gpu_launches": launches,
         "clocks": clocks, "parity": parity, "learned_vs_cost_model": learned,
+        "heavy_product_at_fixed_thresholds": product,
         "extra_workloads": extra,
     }
 

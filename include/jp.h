@@ -169,9 +169,11 @@ typedef struct {
                             fit in half of the free device memory), >= 1 */
 } jp_cost_model;
 
-/* Replace the context's constants (copied; NULL restores the defaults, which were measured on
- * GB300: T_I = 1/60e9, T_m = 1e-12, T_s = 0, mm_rate = 2.2e15, mm_fixed = 2e-5, eps = 0.05,
- * wcoj_factor = 20, judge = 3).  A value out of range gives JP_EINVAL and keeps the old ones. */
+/* Replace the context's constants (copied; NULL restores the defaults: T_I = 0,
+ * T_m = 1.34e-12, T_s = 5.04e-16, mm_rate = 3.85e15, mm_fixed = 1.46e-4, eps = 0.05,
+ * wcoj_factor = 20, judge = 3; the first five fitted by least squares to whole-query times
+ * measured on GB300 over a 7 x 7 grid of fixed thresholds on 789 power-law self-joins of 1e5 to
+ * 5e6 tuples).  A value out of range gives JP_EINVAL and keeps the old ones. */
 int jp_set_cost_model(jp_ctx* ctx, const jp_cost_model* model);
 /* The context's current constants. */
 int jp_get_cost_model(const jp_ctx* ctx, jp_cost_model* model);

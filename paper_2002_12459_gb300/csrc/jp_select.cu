@@ -176,18 +176,23 @@ int64_t clamp_delta(double d, int64_t N) {
 // Default calibration constants of the GPU cost model (seconds), in the
 // roles of Table 2: T_I per light candidate inserted into a deduplication
 // structure, T_m per matrix element / per-x structure set up, T_s per
-// sequential step of the paper's scan of the light-y list for every x (0
-// here: the GPU expansion walks each x's own neighbour list), and the product
-// time model M_hat(u,v,w) = 2uvw / mm_rate + mm_fixed.  Measured on GB300
-// with the 10M power-law self-join: 3.1e9 light candidates in ~50 ms of light
-// kernels, 2.3 PFLOP/s in the product.
+// sequential step of a scan of the light-y list for every x, and the product
+// time model M_hat(u,v,w) = 2uvw / mm_rate + mm_fixed.  They are a
+// non-negative least-squares fit (with a free offset per relation) to
+// whole-query times measured on GB300 at 49 fixed threshold pairs on each of
+// 789 seeded power-law self-joins of 1e5 to 5e6 tuples, over the points
+// within 3x of each relation's fastest.  The fit gives T_I = 0: the bitmap
+// and merge kernels take an extra candidate almost for free (the light cost
+// follows the light-y tuples, the T_s term, and the distinct outputs, which
+// the thresholds do not change), so the heavy product pays only where it
+// removes many light-y tuples.
 jp_cost_model default_cost_model() {
     jp_cost_model K;
-    K.T_I = 1.0 / 60e9;
-    K.T_m = 1.0 / 1.0e12;
-    K.T_s = 0.0;
-    K.mm_rate = 2.2e15;
-    K.mm_fixed = 20e-6;
+    K.T_I = 0.0;
+    K.T_m = 1.34e-12;
+    K.T_s = 5.04e-16;
+    K.mm_rate = 3.85e15;
+    K.mm_fixed = 1.46e-4;
     K.eps = 0.05;
     K.wcoj_factor = 20.0;
     K.judge = 3.0;

@@ -330,8 +330,9 @@ def main(argv=None):
                     help="no sweep: time the held-out relations of a --data file at Algorithm "
                          "3's default constants, at --cost-json's and at --params' predictions")
     ap.add_argument("--params", default=None, help="predictor parameters (.npy) for --compare")
-    ap.add_argument("--cost-json", default=None,
-                    help="fitted cost-model constants (calibrate.py output) for --compare")
+    ap.add_argument("--cost-json", action="append", default=None,
+                    help="cost-model constants ({'constants': ...}, e.g. calibrate.py output) for "
+                         "--compare; repeatable, each an arm named after its file")
     args = ap.parse_args(argv)
 
     from paper_2002_12459_gb300 import build, jp
@@ -345,9 +346,10 @@ def main(argv=None):
         rows = remake_rows([json.loads(str(v)) for v in d["held"]][:args.test])
         ctx = jp.Context(0)
         arms = {"cost_default": ("cost_model", None, None)}
-        if args.cost_json:
-            with open(args.cost_json) as f:
-                arms["cost_fitted"] = ("cost_model", json.load(f)["constants"], None)
+        for path in args.cost_json or []:
+            with open(path) as f:
+                name = "cost_" + os.path.splitext(os.path.basename(path))[0]
+                arms[name] = ("cost_model", json.load(f)["constants"], None)
         pred = None
         if args.params:
             pred = jp.Predictor(0)

@@ -1,15 +1,18 @@
-"""What the shipped threshold predictor gains over the method without it.
+"""What learning from measured threshold sweeps gains over the method's hand-set constants.
 
 Held-out relations (drawn with a seed the training never used, same recipe:
-power-law x and y degrees, exponents uniform in [1.2, 2.5]) are run three
-ways on the GPU: at the cost-model thresholds (Algorithm 3, the method
-without the network), at the predicted thresholds (JP_LEARNED with the
-shipped parameters), and at every point of the threshold grid (the fastest
-is the best-threshold time).  The three give the same tuples; the learned
-path must be within 1.2x the best-threshold time (geometric mean; timing
-noise on small relations makes the bar looser than the 1.1x measured on
-the 48 held-out relations of predictor/report.json), and the learned and
-cost-model times are reported side by side.
+power-law x and y degrees, exponents uniform in [1.2, 2.5]) are run four
+ways on the GPU: at every point of the threshold grid (the fastest is the
+best-threshold time); with Algorithm 3 at the library's default constants
+(fitted to the measured sweeps of 789 relations, predictor/cost_model.json);
+with Algorithm 3 at the constants measured on the 10M relation alone (the
+method without the fit); and at the shipped network's predicted thresholds
+(JP_LEARNED).  All give the same tuples.  On the 256 held-out relations of
+predictor/report.json the fitted constants reach 1.007x the best-grid time,
+the single-relation constants 1.109x and the network 1.10x; here, on six
+small relations where timing noise is larger, the fitted constants must stay
+within 1.15x of the best and not lose to the single-relation constants, and
+the network within 1.2x.
 """
 import math
 
@@ -17,6 +20,8 @@ import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
+
+SINGLE = dict(T_I=1.0 / 60e9, T_m=1e-12, T_s=0.0, mm_rate=2.2e15, mm_fixed=2e-5)
 
 
 @pytest.fixture(scope="module")
@@ -33,20 +38,25 @@ def env():
     pred = jp.Predictor.trained(0)
     yield ctx, pred, specs, learn
     ctx.set_predictor(None)
+    ctx.set_cost_model()
     pred.close()
     ctx.close()
 
 
-def test_learned_thresholds_against_best_and_cost_model(env):
+def test_fitted_constants_and_learned_thresholds_against_best(env):
     import torch
     ctx, pred, specs, learn = env
     rows = []
     for spec, x, y in specs:
         dx, dy = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
         ctx.set_predictor(None)
+        ctx.set_cost_model()
         ctx.set_threshold("cost_model")
         cx, cz = ctx.two_path(dx, dy)
-        t_cost = learn.query_ms(ctx, dx, dy, "cost_model", reps=3)[0]
+        t_fit = learn.query_ms(ctx, dx, dy, "cost_model", reps=3)[0]
+        ctx.set_cost_model(**SINGLE)
+        t_single = learn.query_ms(ctx, dx, dy, "cost_model", reps=3)[0]
+        ctx.set_cost_model()
         ctx.set_predictor(pred)
         ctx.set_threshold("learned")
         lx, lz = ctx.two_path(dx, dy)
@@ -58,12 +68,17 @@ def test_learned_thresholds_against_best_and_cost_model(env):
         times = learn.sweep(ctx, dx, dy, x, y)
         t_best = min(times.values())
         assert math.isfinite(t_best)
-        rows.append((spec["n"], t_best, t_cost, t_learn, (st["delta1"], st["delta2"])))
+        rows.append((spec["n"], t_best, t_fit, t_single, t_learn))
         del cx, cz, lx, lz
-    g_learn = float(np.exp(np.mean([np.log(r[3] / r[1]) for r in rows])))
-    g_cost = float(np.exp(np.mean([np.log(r[2] / r[1]) for r in rows])))
+
+    def g(i):
+        return float(np.exp(np.mean([np.log(r[i] / r[1]) for r in rows])))
+
+    g_fit, g_single, g_learn = g(2), g(3), g(4)
     for r in rows:
-        print(f"N={r[0]} best {r[1]:.3f} ms  cost-model {r[2]:.3f} ms  learned {r[3]:.3f} ms "
-              f"(delta {r[4]})")
-    print(f"learned/best {g_learn:.3f}  cost-model/best {g_cost:.3f}")
-    assert g_learn <= 1.2, (g_learn, g_cost)
+        print(f"N={r[0]} best {r[1]:.3f} ms  fitted {r[2]:.3f}  single-relation {r[3]:.3f}  "
+              f"learned {r[4]:.3f}")
+    print(f"over best: fitted {g_fit:.3f}  single-relation {g_single:.3f}  learned {g_learn:.3f}")
+    assert g_fit <= 1.15, (g_fit, g_single, g_learn)
+    assert g_fit <= g_single + 0.02, (g_fit, g_single)
+    assert g_learn <= 1.2, (g_learn, g_fit)

@@ -84,6 +84,8 @@ def _oracle_of(rel):
 # (cheap product: deep descent; light work nearly free: shallow; T_s and T_m weighted).
 CONSTS = [
     None,
+    # the constants measured on the 10M relation alone (the earlier defaults)
+    dict(T_I=1.0 / 60e9, T_m=1e-12, T_s=0.0, mm_rate=2.2e15, mm_fixed=2e-5, eps=0.05),
     dict(T_I=1e-10, T_m=1e-12, T_s=0.0, mm_rate=1e17, mm_fixed=0.0, eps=0.05),
     dict(T_I=1e-13, T_m=1e-12, T_s=0.0, mm_rate=1e13, mm_fixed=1e-3, eps=0.05),
     dict(T_I=2e-11, T_m=5e-11, T_s=1e-14, mm_rate=3e15, mm_fixed=5e-5, eps=0.1),
@@ -146,6 +148,20 @@ def test_algorithm3_thresholds(ctx, name, ci):
     assert (st["u"], st["v"], st["w"]) == (idx.heavy_x(d2), idx.heavy_y(d1), idx.heavy_z(d2))
     if how == "mm":
         assert len(tr) >= 2
+
+
+def test_default_constants_are_the_shipped_fit(ctx):
+    """The library's default constants are the calibration recorded in predictor/cost_model.json
+    (rounded to three significant digits)."""
+    import json
+    import os
+    from paper_2002_12459_gb300 import calibrate
+    with open(os.path.join(calibrate.PKG, "predictor", "cost_model.json")) as f:
+        fit = json.load(f)["constants"]
+    ctx.set_cost_model()
+    K = ctx.cost_model()
+    for k, v in fit.items():
+        assert K[k] == pytest.approx(v, rel=5e-3, abs=1e-30), k
 
 
 def test_cost_model_constants_are_checked(ctx):
