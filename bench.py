@@ -931,7 +931,7 @@ def run_ssj(args):
                    "order": "count descending, ties in (x, z) order",
                    "query": "SSJ: (a, c, |R[a] ∩ R[c]|) with |R[a] ∩ R[c]| >= c_min",
                    "threshold_mode": args.mode, "delta1": st["delta1"], "delta2": st["delta2"],
-                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": total_out,
+                   "u": st["u"], "v": st["v"], "w": st["w"], "out_count": out,
                    "light_candidates": st["light_candidates"], "x_ranges": st["count_ranges"],
                    "light_pairs": st["count_light_pairs"], "heavy_pairs": st["heavy_pairs"],
                    "l2": "256 MiB flush written before every step",
