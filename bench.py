@@ -309,12 +309,15 @@ KERNEL_SLOTS = {4: "heavy_gemm_kernel", 6: "light_warp_kernel<256>",
 SLOT_CLASS = {6: (0,), 7: (1,), 8: (4, 5, 7), 9: (3, 6)}
 
 # DRAM bytes (read + write) of one launch, from one ncu capture of the bench
-# workload (profiles/light_bitmap_kernel_powerlaw_10m_dram.md); reported only
-# while the kernel's source file is the one that was captured
+# workload at the default thresholds (profiles/bitmap_and_place_powerlaw_10m_dram.md);
+# reported only while the kernel's source file is the one that was captured
 MEASURED_TRAFFIC = {
-    "light_bitmap_kernel": {"bytes": 1540441344 + 5362752768, "workload": "two_path_powerlaw_10m",
+    "light_bitmap_kernel": {"bytes": 1165531648 + 5173207552, "workload": "two_path_powerlaw_10m",
                             "source": "paper_2002_12459_gb300/csrc/jp_light.cu",
-                            "sha1": "b69b31a681b4a4a0740532911bfa9b85bb90e26d"},
+                            "sha1": "e29ade766810369c98b3bb04bd020f04c317e9cf"},
+    "place_kernel": {"bytes": 11696101376 + 24418124032, "workload": "two_path_powerlaw_10m",
+                     "source": "paper_2002_12459_gb300/csrc/jp_output.cu",
+                     "sha1": "1782dbbedff35191b7ba2140a72f239466c9c00c"},
 }
 
 

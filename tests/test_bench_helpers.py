@@ -97,14 +97,15 @@ def test_ssj_rooflines_pick_the_slowest_phase():
     assert per["cand_fill_kernel"]["achieved"] == pytest.approx(12.0 * 175 / 0.2e-3 / 1e9)
 
 
-def test_traffic_is_reported_only_for_the_captured_source():
-    m = bench.MEASURED_TRAFFIC["light_bitmap_kernel"]
+@pytest.mark.parametrize("kernel", ["light_bitmap_kernel", "place_kernel"])
+def test_traffic_is_reported_only_for_the_captured_source(kernel):
+    m = bench.MEASURED_TRAFFIC[kernel]
     src = open(os.path.join(bench.ROOT, m["source"]), "rb").read()
     same = hashlib.sha1(src).hexdigest() == m["sha1"]
-    got = bench.measured_traffic("light_bitmap_kernel", m["workload"])
+    got = bench.measured_traffic(kernel, m["workload"])
     assert got == (m["bytes"] if same else None)
-    assert bench.measured_traffic("light_bitmap_kernel", "star3_2m") is None
-    assert bench.measured_traffic("place_kernel", m["workload"]) is None
+    assert bench.measured_traffic(kernel, "star3_2m") is None
+    assert bench.measured_traffic("light_merge_kernel", m["workload"]) is None
 
 
 class _Proc:
