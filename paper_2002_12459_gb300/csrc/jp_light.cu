@@ -740,6 +740,40 @@ __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t* own
     if (!(old & bit)) atomicAdd(&own[wi >> owner_shift], 1u);
 }
 
+// Marking of one chunk of a row's lists: flat candidate f belongs to the last
+// list k with s_pre[k] <= f, found by a STEPS-step binary search (the chunk
+// has at most 2^STEPS lists; entries past them hold the total).  Each thread
+// loads U candidates before it marks any.
+constexpr bool BM_TIERED = true;
+template <int STEPS>
+__device__ __forceinline__ void mark_chunk(const LightArgs& A, const uint32_t* s_pre,
+                                           const int32_t* s_start, uint32_t total, int64_t z0,
+                                           int64_t zend, uint32_t* bm, uint32_t* summ,
+                                           uint32_t* own, int owner_shift) {
+    constexpr int U = 8;
+    for (uint32_t f0 = threadIdx.x; f0 < total; f0 += U * BM_THREADS) {
+        int32_t zz[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t f = f0 + (uint32_t)u * BM_THREADS;
+            zz[u] = -1;
+            if (f < total) {
+                int32_t k = 0;      // last k with s_pre[k] <= f (s_pre[0] = 0)
+#pragma unroll
+                for (int step = 1 << (STEPS - 1); step > 0; step >>= 1)
+                    if (s_pre[k + step] <= f) k += step;
+                const int32_t st0 = s_start[k];
+                const uint32_t off = f - s_pre[k];
+                zz[u] = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (zz[u] >= z0 && zz[u] < zend)
+                mark(bm, summ, own, owner_shift, (int32_t)(zz[u] - z0));
+    }
+}
+
 // Exclusive prefix over a 1024-thread block; *total gets the block's sum.
 // Two barriers; sw holds 32 words.
 __device__ __forceinline__ uint32_t bm_block_scan(uint32_t v, uint32_t* sw, uint32_t* total) {
@@ -797,6 +831,7 @@ __device__ __forceinline__ int run_owner(uint32_t ex, uint32_t j) {
 // walking its own words; denser rows by warps, each over the words of its 32
 // threads, 32 words at a time with coalesced stores.
 constexpr int BM_CHUNK = 1024;           // neighbour lists per marking chunk
+static_assert(BM_CHUNK == 1 << 10, "the deepest marking search (10 steps) covers one chunk");
 constexpr uint32_t BM_DENSE = 160000;    // rows with more values are emitted by warps
 
 __global__ void __launch_bounds__(BM_THREADS, 1)
@@ -869,28 +904,14 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 s_pre[threadIdx.x] = (int32_t)threadIdx.x < n ? ex : total;
                 s_start[threadIdx.x] = bl.x;
                 __syncthreads();
-                constexpr int U = 8;    // candidates loaded before any is marked
-                for (uint32_t f0 = threadIdx.x; f0 < total; f0 += U * BM_THREADS) {
-                    int32_t zz[U];
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const uint32_t f = f0 + (uint32_t)u * BM_THREADS;
-                        zz[u] = -1;
-                        if (f < total) {
-                            int32_t k = 0;      // last k with s_pre[k] <= f (s_pre[0] = 0)
-#pragma unroll
-                            for (int step = BM_CHUNK / 2; step > 0; step >>= 1)
-                                if (s_pre[k + step] <= f) k += step;
-                            const int32_t st0 = s_start[k];
-                            const uint32_t off = f - s_pre[k];
-                            zz[u] = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        if (zz[u] >= z0 && zz[u] < zend)
-                            mark(bm, summ, own, owner_shift, (int32_t)(zz[u] - z0));
-                }
+                // the search needs log2 of the chunk's list count rounded up
+                // to a power of two: three unrolled depths
+                if (BM_TIERED && n <= 32)
+                    mark_chunk<5>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
+                else if (BM_TIERED && n <= 256)
+                    mark_chunk<8>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
+                else
+                    mark_chunk<10>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
                 __syncthreads();        // s_pre / s_start are rewritten by the next chunk
             }
             // ---- heavy product row, 32 words per warp step
