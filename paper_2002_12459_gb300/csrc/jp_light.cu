@@ -774,6 +774,59 @@ __device__ __forceinline__ void mark_chunk(const LightArgs& A, const uint32_t* s
     }
 }
 
+// The same marking with each warp on one contiguous run of the chunk's
+// candidates: lane i takes candidates run_start + i, + 32, ..., so a lane's
+// list only moves forward.  The lane keeps its list's bounds in registers and
+// reads shared memory only when a candidate is past them: one step forward
+// when the next list holds it, else a search.
+constexpr bool BM_WALK = true;
+template <int STEPS>
+__device__ __forceinline__ int32_t chunk_list(const uint32_t* s_pre, uint32_t f) {
+    int32_t k = 0;      // last k with s_pre[k] <= f (s_pre[0] = 0)
+#pragma unroll
+    for (int step = 1 << (STEPS - 1); step > 0; step >>= 1)
+        if (s_pre[k + step] <= f) k += step;
+    return k;
+}
+template <int STEPS>
+__device__ __forceinline__ void mark_chunk_walk(const LightArgs& A, const uint32_t* s_pre,
+                                                const int32_t* s_start, uint32_t total,
+                                                int64_t z0, int64_t zend, uint32_t* bm,
+                                                uint32_t* summ, uint32_t* own, int owner_shift) {
+    constexpr int U = 8, NW = BM_THREADS / 32, LAST = (1 << STEPS) - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = ((total + NW - 1) / NW + 31) & ~31u;
+    const uint32_t fb = min(total, (uint32_t)warp * per), fe = min(total, fb + per);
+    if (fb + lane >= fe) return;
+    // entries past the chunk's lists hold the total, so pn = total past the last list
+    int32_t k = chunk_list<STEPS>(s_pre, fb + lane);
+    uint32_t pk = s_pre[k], pn = k < LAST ? s_pre[k + 1] : total;
+    int32_t sk = s_start[k];
+    for (uint32_t g = fb + lane; g < fe; g += 32 * U) {
+        int32_t zz[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t f = g + 32u * (uint32_t)u;
+            zz[u] = -1;
+            if (f < fe) {
+                if (f >= pn) {
+                    const uint32_t p2 = k + 1 < LAST ? s_pre[k + 2] : total;
+                    k = f < p2 ? k + 1 : chunk_list<STEPS>(s_pre, f);
+                    pk = s_pre[k];
+                    pn = k < LAST ? s_pre[k + 1] : total;
+                    sk = s_start[k];
+                }
+                const uint32_t off = f - pk;
+                zz[u] = sk >= 0 ? A.szcol[sk + off] : A.slcol[-sk - 1 + off];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (zz[u] >= z0 && zz[u] < zend)
+                mark(bm, summ, own, owner_shift, (int32_t)(zz[u] - z0));
+    }
+}
+
 // Exclusive prefix over a 1024-thread block; *total gets the block's sum.
 // Two barriers; sw holds 32 words.
 __device__ __forceinline__ uint32_t bm_block_scan(uint32_t v, uint32_t* sw, uint32_t* total) {
@@ -906,7 +959,17 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 __syncthreads();
                 // the search needs log2 of the chunk's list count rounded up
                 // to a power of two: three unrolled depths
-                if (BM_TIERED && n <= 32)
+                if (BM_WALK) {
+                    if (n <= 32)
+                        mark_chunk_walk<5>(A, s_pre, s_start, total, z0, zend, bm, summ, own,
+                                           owner_shift);
+                    else if (n <= 256)
+                        mark_chunk_walk<8>(A, s_pre, s_start, total, z0, zend, bm, summ, own,
+                                           owner_shift);
+                    else
+                        mark_chunk_walk<10>(A, s_pre, s_start, total, z0, zend, bm, summ, own,
+                                            owner_shift);
+                } else if (BM_TIERED && n <= 32)
                     mark_chunk<5>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
                 else if (BM_TIERED && n <= 256)
                     mark_chunk<8>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
