@@ -24,6 +24,10 @@ __global__ void widen_kernel(const int32_t* in, int64_t n, int64_t* out) {
 }
 
 constexpr int OUT_SX = 512;   // x entries staged in shared memory per tile
+// staged tiles: a thread's outputs (OUT_THREADS apart) only move forward
+// through the rows, so it keeps its current row's bounds and values in
+// registers and reads shared memory again only past the row's end
+constexpr bool OUT_WALK = true;
 
 // largest x in [lo, hi) with off[x] <= o (off non-decreasing, off[lo] <= o)
 __device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_t hi, int64_t o) {
@@ -65,12 +69,11 @@ __global__ void tile_start_kernel(const int64_t* __restrict__ out_off, int64_t n
 // X2: a second row column (the star's x2) is written next to the first.
 // VMAP: x and z values are ids into vmap, which gives the written values.
 // Bound by latency: a thread's loads are the only work in flight, so the
-// launch bound asks for 8 resident blocks per SM (2,048 threads, at most 32
-// registers each); measured faster than 5 or 6 blocks per SM.  The two-column
-// form (X2, the star query's rows) holds more per output: 6 blocks per SM
-// measured faster for it than 8 or the compiler's own choice.
+// launch bound asks for 6 resident blocks per SM (1,536 threads, at most 40
+// registers each).  With the row walk, 8 blocks per SM (32 registers) spill
+// and measured slower; without it 8 was the best.
 template <bool X2, bool VMAP>
-__global__ void __launch_bounds__(OUT_THREADS, X2 ? 6 : 8)
+__global__ void __launch_bounds__(OUT_THREADS, 6)
     place_kernel(const int64_t* __restrict__ out_off, int64_t nx,
                              const int32_t* __restrict__ tile_x,
                              const int64_t* __restrict__ tmp_off, const int32_t* __restrict__ tmp,
@@ -105,6 +108,8 @@ __global__ void __launch_bounds__(OUT_THREADS, X2 ? 6 : 8)
     // the stores: OUT_VT independent loads in flight per phase
     int32_t zv[OUT_VT], xv[OUT_VT], xv2[OUT_VT];
     uint32_t ids = 0;   // bit k: zv[k] is a z id
+    int64_t ri = -1, r_beg = 0, r_end = -1, r_toff = 0;   // the current staged row
+    int32_t r_xv = 0, r_xv2 = 0;
 #pragma unroll
     for (int k = 0; k < OUT_VT; ++k) {
         const int64_t o = o0 + threadIdx.x + (int64_t)k * OUT_THREADS;
@@ -113,7 +118,23 @@ __global__ void __launch_bounds__(OUT_THREADS, X2 ? 6 : 8)
         xv2[k] = 0;
         bool is_id = false;
         if (o <= o_last) {
-            if (staged) {
+            if (staged && OUT_WALK) {
+                if (o >= r_end) {
+                    // the next row when it holds o, else a search past the current one
+                    const int64_t i = (ri >= 0 && ri + 2 <= nxs && o < s_off[ri + 2])
+                                          ? ri + 1
+                                          : find_x(s_off, ri < 0 ? 0 : ri + 1, nxs, o);
+                    ri = i;
+                    r_beg = s_off[i];
+                    r_end = s_off[i + 1];
+                    r_toff = s_toff[i];
+                    r_xv = s_xv[i];
+                    if (X2) r_xv2 = s_xv2[i];
+                }
+                zv[k] = list_at(tmp, szval, r_toff, o - r_beg, &is_id);
+                xv[k] = r_xv;
+                if (X2) xv2[k] = r_xv2;
+            } else if (staged) {
                 const int64_t i = find_x(s_off, 0, nxs, o);
                 zv[k] = list_at(tmp, szval, s_toff[i], o - s_off[i], &is_id);
                 xv[k] = s_xv[i];
