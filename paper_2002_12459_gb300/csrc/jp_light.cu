@@ -616,7 +616,10 @@ __global__ void __launch_bounds__(TPB)
         // gather: flat candidate f of run k is S[b_k][f - run_k]; a thread's f
         // only grow, so its run index k only moves forward
         constexpr int U = 8;
+        // the thread's current run: [r_beg, r_end) starting at S offset r_st,
+        // kept in registers (shared memory is read only at run boundaries)
         int k = 0;
+        int32_t r_beg = 0, r_end = s_runs[0][1], r_st = s_start[0];
         for (int32_t f0 = tid; f0 < c; f0 += U * TPB) {
             int32_t zz[U];
 #pragma unroll
@@ -624,8 +627,13 @@ __global__ void __launch_bounds__(TPB)
                 const int32_t f = f0 + u * TPB;
                 zz[u] = 0;
                 if (f < c) {
-                    while (s_runs[0][k + 1] <= f) ++k;
-                    zz[u] = A.szval[s_start[k] + (f - s_runs[0][k])];
+                    while (r_end <= f) {
+                        ++k;
+                        r_beg = r_end;
+                        r_end = s_runs[0][k + 1];
+                        r_st = s_start[k];
+                    }
+                    zz[u] = A.szval[r_st + (f - r_beg)];
                 }
             }
 #pragma unroll
