@@ -734,9 +734,8 @@ __global__ void __launch_bounds__(TPB)
 // 32-word groups at the same time, and this spreads them over the 32 banks
 // (without it every lane reads bank j).  A warp reading a whole 32-word
 // group reads a permutation of it, also conflict-free.
-constexpr bool BM_SWZ = true;
 __device__ __forceinline__ int32_t bm_at(int32_t wi, int owner_shift) {
-    return BM_SWZ ? (wi ^ ((wi >> owner_shift) & 31)) : wi;
+    return wi ^ ((wi >> owner_shift) & 31);
 }
 
 __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t* own, int owner_shift,
@@ -748,46 +747,14 @@ __device__ __forceinline__ void mark(uint32_t* bm, uint32_t* summ, uint32_t* own
     if (!(old & bit)) atomicAdd(&own[wi >> owner_shift], 1u);
 }
 
-// Marking of one chunk of a row's lists: flat candidate f belongs to the last
-// list k with s_pre[k] <= f, found by a STEPS-step binary search (the chunk
-// has at most 2^STEPS lists; entries past them hold the total).  Each thread
-// loads U candidates before it marks any.
-constexpr bool BM_TIERED = true;
-template <int STEPS>
-__device__ __forceinline__ void mark_chunk(const LightArgs& A, const uint32_t* s_pre,
-                                           const int32_t* s_start, uint32_t total, int64_t z0,
-                                           int64_t zend, uint32_t* bm, uint32_t* summ,
-                                           uint32_t* own, int owner_shift) {
-    constexpr int U = 8;
-    for (uint32_t f0 = threadIdx.x; f0 < total; f0 += U * BM_THREADS) {
-        int32_t zz[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t f = f0 + (uint32_t)u * BM_THREADS;
-            zz[u] = -1;
-            if (f < total) {
-                int32_t k = 0;      // last k with s_pre[k] <= f (s_pre[0] = 0)
-#pragma unroll
-                for (int step = 1 << (STEPS - 1); step > 0; step >>= 1)
-                    if (s_pre[k + step] <= f) k += step;
-                const int32_t st0 = s_start[k];
-                const uint32_t off = f - s_pre[k];
-                zz[u] = st0 >= 0 ? A.szcol[st0 + off] : A.slcol[-st0 - 1 + off];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (zz[u] >= z0 && zz[u] < zend)
-                mark(bm, summ, own, owner_shift, (int32_t)(zz[u] - z0));
-    }
-}
-
-// The same marking with each warp on one contiguous run of the chunk's
-// candidates: lane i takes candidates run_start + i, + 32, ..., so a lane's
-// list only moves forward.  The lane keeps its list's bounds in registers and
-// reads shared memory only when a candidate is past them: one step forward
-// when the next list holds it, else a search.
-constexpr bool BM_WALK = true;
+// Marking of one chunk of a row's lists.  Flat candidate f belongs to the
+// last list k with s_pre[k] <= f (a STEPS-step binary search: the chunk has at
+// most 2^STEPS lists, and entries past them hold the total).  Each warp takes
+// one contiguous run of the chunk's candidates, lane i the candidates
+// run_start + i, + 32, ..., so a lane's list only moves forward: the lane keeps
+// its list's bounds in registers and reads shared memory only when a
+// candidate is past them (one step forward when the next list holds it, else
+// the search).  Each thread loads U candidates before it marks any.
 template <int STEPS>
 __device__ __forceinline__ int32_t chunk_list(const uint32_t* s_pre, uint32_t f) {
     int32_t k = 0;      // last k with s_pre[k] <= f (s_pre[0] = 0)
@@ -797,10 +764,10 @@ __device__ __forceinline__ int32_t chunk_list(const uint32_t* s_pre, uint32_t f)
     return k;
 }
 template <int STEPS>
-__device__ __forceinline__ void mark_chunk_walk(const LightArgs& A, const uint32_t* s_pre,
-                                                const int32_t* s_start, uint32_t total,
-                                                int64_t z0, int64_t zend, uint32_t* bm,
-                                                uint32_t* summ, uint32_t* own, int owner_shift) {
+__device__ __forceinline__ void mark_chunk(const LightArgs& A, const uint32_t* s_pre,
+                                           const int32_t* s_start, uint32_t total, int64_t z0,
+                                           int64_t zend, uint32_t* bm, uint32_t* summ,
+                                           uint32_t* own, int owner_shift) {
     constexpr int U = 8, NW = BM_THREADS / 32, LAST = (1 << STEPS) - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t per = ((total + NW - 1) / NW + 31) & ~31u;
@@ -967,19 +934,9 @@ __global__ void __launch_bounds__(BM_THREADS, 1)
                 __syncthreads();
                 // the search needs log2 of the chunk's list count rounded up
                 // to a power of two: three unrolled depths
-                if (BM_WALK) {
-                    if (n <= 32)
-                        mark_chunk_walk<5>(A, s_pre, s_start, total, z0, zend, bm, summ, own,
-                                           owner_shift);
-                    else if (n <= 256)
-                        mark_chunk_walk<8>(A, s_pre, s_start, total, z0, zend, bm, summ, own,
-                                           owner_shift);
-                    else
-                        mark_chunk_walk<10>(A, s_pre, s_start, total, z0, zend, bm, summ, own,
-                                            owner_shift);
-                } else if (BM_TIERED && n <= 32)
+                if (n <= 32)
                     mark_chunk<5>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
-                else if (BM_TIERED && n <= 256)
+                else if (n <= 256)
                     mark_chunk<8>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);
                 else
                     mark_chunk<10>(A, s_pre, s_start, total, z0, zend, bm, summ, own, owner_shift);

@@ -24,10 +24,6 @@ __global__ void widen_kernel(const int32_t* in, int64_t n, int64_t* out) {
 }
 
 constexpr int OUT_SX = 512;   // x entries staged in shared memory per tile
-// staged tiles: a thread's outputs (OUT_THREADS apart) only move forward
-// through the rows, so it keeps its current row's bounds and values in
-// registers and reads shared memory again only past the row's end
-constexpr bool OUT_WALK = true;
 
 // largest x in [lo, hi) with off[x] <= o (off non-decreasing, off[lo] <= o)
 __device__ __forceinline__ int64_t find_x(const int64_t* off, int64_t lo, int64_t hi, int64_t o) {
@@ -118,7 +114,10 @@ __global__ void __launch_bounds__(OUT_THREADS, 6)
         xv2[k] = 0;
         bool is_id = false;
         if (o <= o_last) {
-            if (staged && OUT_WALK) {
+            if (staged) {
+                // a thread's outputs (OUT_THREADS apart) only move forward through
+                // the rows: it keeps its current row's bounds and values in
+                // registers and reads shared memory again only past the row's end
                 if (o >= r_end) {
                     // the next row when it holds o, else a search past the current one
                     const int64_t i = (ri >= 0 && ri + 2 <= nxs && o < s_off[ri + 2])
@@ -134,11 +133,6 @@ __global__ void __launch_bounds__(OUT_THREADS, 6)
                 zv[k] = list_at(tmp, szval, r_toff, o - r_beg, &is_id);
                 xv[k] = r_xv;
                 if (X2) xv2[k] = r_xv2;
-            } else if (staged) {
-                const int64_t i = find_x(s_off, 0, nxs, o);
-                zv[k] = list_at(tmp, szval, s_toff[i], o - s_off[i], &is_id);
-                xv[k] = s_xv[i];
-                if (X2) xv2[k] = s_xv2[i];
             } else {
                 const int64_t x = find_x(out_off, xlo, xhi, o);
                 zv[k] = list_at(tmp, szval, tmp_off[x], o - out_off[x], &is_id);
