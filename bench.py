@@ -312,12 +312,12 @@ SLOT_CLASS = {6: (0,), 7: (1,), 8: (4, 5, 7), 9: (3, 6)}
 # workload at the default thresholds (profiles/bitmap_and_place_powerlaw_10m_dram.md);
 # reported only while the kernel's source file is the one that was captured
 MEASURED_TRAFFIC = {
-    "light_bitmap_kernel": {"bytes": 1237688576 + 5220552704, "workload": "two_path_powerlaw_10m",
+    "light_bitmap_kernel": {"bytes": 1241229568 + 5222891776, "workload": "two_path_powerlaw_10m",
                             "source": "paper_2002_12459_gb300/csrc/jp_light.cu",
-                            "sha1": "6e1ced76686e24030260c16d02e498518d27a261"},
-    "place_kernel": {"bytes": 11680976384 + 23197939712, "workload": "two_path_powerlaw_10m",
+                            "sha1": "95c8ccdfe846de4ef4dac21c2da142611c21ac10"},
+    "place_kernel": {"bytes": 11679594496 + 23196820736, "workload": "two_path_powerlaw_10m",
                      "source": "paper_2002_12459_gb300/csrc/jp_output.cu",
-                     "sha1": "d23f5abc212600ca6c31e6a5682ba59efdc89962"},
+                     "sha1": "0a4f08bc2e83946a3f124a9c9c4b2af1752f312c"},
 }
 
 
