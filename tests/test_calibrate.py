@@ -63,3 +63,32 @@ def test_fit_recovers_planted_constants():
     c = calibrate.constants(k, calibrate.DEFAULT_BASE)
     assert math.isclose(c["mm_rate"], 3e15, rel_tol=1e-4)
     assert c["eps"] == calibrate.DEFAULT_BASE["eps"]
+
+
+def test_end_to_end_on_a_saved_sweep(tmp_path):
+    """load_rows -> design -> fit on a tiny sweep file written like learn.py's --data output:
+    three seeded relations whose grid times are made from known constants."""
+    import json
+    from paper_2002_12459_gb300 import learn
+    k_true = np.array([1.0 / 100e9, 0.0, 1.0 / 2e15, 50e-6, 1.0 / 8e11])
+    rows = []
+    for i in range(3):
+        spec = learn.relation_spec(i, seed=11, n_lo=2e4, n_hi=4e4)
+        x, y = learn.make_relation(spec)
+        degx, degy, cand, _ = calibrate.degree_terms(x, y)
+        grid = [[1e3 * (2e-3 + float(np.dot(k_true, calibrate.features(degx, degy, cand, d1, d2))))
+                 for d2 in learn.D2_GRID] for d1 in learn.D1_GRID]
+        grid[0][0] = math.inf                     # a skipped grid point
+        rows.append(dict(spec=spec, grid=grid))
+    path = tmp_path / "sweeps.npz"
+    meta = np.array([json.dumps(r) for r in rows])
+    np.savez(path, train=meta, held=meta[:1], d1_grid=np.array(learn.D1_GRID),
+             d2_grid=np.array(learn.D2_GRID))
+    got = calibrate.load_rows(str(path))
+    assert len(got) == 3 and got[0]["d1_grid"] == list(learn.D1_GRID)
+    F, t, grp = calibrate.design(got, workers=2)
+    assert len(t) == 3 * (49 - 1) and set(grp.tolist()) == {0, 1, 2}
+    k, rms, rms0 = calibrate.fit(F, t, grp)
+    assert rms < 1e-6 * rms0
+    assert math.isclose(k[0], k_true[0], rel_tol=1e-3)
+    assert math.isclose(1.0 / k[2], 2e15, rel_tol=1e-3)
