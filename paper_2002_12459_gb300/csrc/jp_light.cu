@@ -850,11 +850,12 @@ __device__ __forceinline__ int run_owner(uint32_t ex, uint32_t j) {
 // each thread knows its run's length without a pass over the bitmap.
 //
 // Marking: the row's neighbour lists are taken 1024 at a time, one per
-// thread (bounds from the per-y tables, prefix-summed over the block); thread
-// t then takes flat candidates t, t + 1024, ... (adjacent threads read
-// adjacent list entries) and finds each one's list by a 10-step search over
-// the chunk's prefix sums.  A heavy row's product row (bit l of G means
-// (a, hz_inv[l]) is an output) is expanded by all warps, 32 words at a time.
+// thread (bounds from the per-y tables, prefix-summed over the block); each
+// warp then marks a contiguous run of the chunk's flat candidates (adjacent
+// lanes read adjacent list entries), each lane holding its current list's
+// bounds in registers (mark_chunk).  A heavy row's product row (bit l of G
+// means (a, hz_inv[l]) is an output) is expanded by all warps, 32 words at a
+// time.
 // Emission: rows with up to BM_DENSE values are written by each thread
 // walking its own words; denser rows by warps, each over the words of its 32
 // threads, 32 words at a time with coalesced stores.

@@ -1,6 +1,5 @@
 """Host logic of bench.py (no GPU): the oracle sample, the roofline arithmetic, the traffic
 gate and the clock record."""
-import hashlib
 import os
 
 import numpy as np
@@ -100,12 +99,22 @@ def test_ssj_rooflines_pick_the_slowest_phase():
 @pytest.mark.parametrize("kernel", ["light_bitmap_kernel", "place_kernel"])
 def test_traffic_is_reported_only_for_the_captured_source(kernel):
     m = bench.MEASURED_TRAFFIC[kernel]
-    src = open(os.path.join(bench.ROOT, m["source"]), "rb").read()
-    same = hashlib.sha1(src).hexdigest() == m["sha1"]
+    same = bench.code_hash(os.path.join(bench.ROOT, m["source"])) == m["code_sha1"]
     got = bench.measured_traffic(kernel, m["workload"])
     assert got == (m["bytes"] if same else None)
     assert bench.measured_traffic(kernel, "star3_2m") is None
     assert bench.measured_traffic("light_merge_kernel", m["workload"]) is None
+
+
+def test_code_hash_ignores_comments_only(tmp_path):
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("// one\nint f(int x) {  /* add */ return x + 1; }\n")
+    b.write_text("// two, longer\nint f(int x) {\n    return x + 1;  // add\n}\n")
+    c.write_text("int f(int x) { return x + 2; }\n")
+    assert bench.code_hash(str(a)) == bench.code_hash(str(b))
+    assert bench.code_hash(str(a)) != bench.code_hash(str(c))
 
 
 class _Proc:
